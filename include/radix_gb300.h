@@ -1,0 +1,179 @@
+/*
+ * radix_gb300 — MSD radix sorting of fixed-size records on one GPU (sm_103a).
+ *
+ * The method is RADULS2 (M. Kokot, S. Deorowicz, M. Dlugosz, "Even faster sorting of
+ * (not only) integers", 2017), re-designed for the GPU.  Section 1 of the paper states the
+ * problem (order records by a key made of digits; radix sort processes one digit per phase
+ * with a counting sort), section 3.1 the method (an MSD radix sort with 1-byte digits:
+ * distribute the whole array by the first digit, then process the bins independently, and
+ * hand tiny bins to a dedicated sorter), sections 3.2-3.3 the small- and tiny-bin steps.
+ *
+ * Records.  A record is rec_size bytes (a multiple of 8, at most 256).  Its key is bytes
+ * [0, key_size) read as a little-endian unsigned integer (1 <= key_size <= 16, and
+ * key_size <= rec_size): byte key_size-1 is the most significant, so for key_size = 8 the key
+ * is the native uint64 at offset 0, and for key_size = 16 the word at bytes 8..15 is compared
+ * before the word at bytes 0..7.  The other bytes are data that moves with the key.
+ *
+ * Order.  The result is the stable sort by key: keys are non-decreasing and records with
+ * equal keys keep their input order.  It is therefore unique and byte-identical to a stable
+ * LSD radix sort of the same records.
+ *
+ * Memory.  All record buffers are device memory owned by the caller; the library never
+ * allocates, frees or keeps them.  The library owns a metadata workspace per (device,
+ * stream) — histograms, bucket bases, bin and chunk lists, look-back words, a status word —
+ * allocated on first use with cudaMalloc (so the first call for a given size must not be
+ * made while the stream is being captured into a CUDA graph), grown when a larger call
+ * needs it, reused, and freed by radix_sort_release().
+ *
+ * Asynchrony.  Every call validates its arguments on the host and returns at once; the
+ * work runs asynchronously on `stream` (NULL = the legacy default stream).  Errors found on
+ * the device (a look-back wait that hit its limit, a list that overflowed) set the status
+ * word and are reported by radix_sort_status() after the stream has drained; no kernel
+ * traps or waits without a bound.  Calls on one stream run in order; calls on different
+ * streams use different workspaces and may overlap.
+ *
+ * Errors.  A call that returns anything but RS_OK launched no work.
+ */
+#ifndef RADIX_GB300_H
+#define RADIX_GB300_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+struct CUstream_st;
+typedef struct CUstream_st *rs_stream_t; /* a cudaStream_t */
+
+typedef enum rs_status {
+  RS_OK = 0,
+  RS_ERR_INVALID_ARG = 1,    /* a size or pointer argument is out of range */
+  RS_ERR_MISALIGNED = 2,     /* a record buffer is not 16-byte aligned */
+  RS_ERR_OVERLAP = 3,        /* the two record buffers overlap */
+  RS_ERR_TOO_LARGE = 4,      /* n * rec_size does not fit in 64 bits / in the address space */
+  RS_ERR_NO_MEMORY = 5,      /* the workspace could not be allocated */
+  RS_ERR_CUDA = 6,           /* a CUDA runtime call failed (launch, memcpy, sync) */
+  RS_ERR_DEVICE_TIMEOUT = 7, /* a device-side wait hit its limit (result undefined) */
+  RS_ERR_QUEUE_OVERFLOW = 8, /* a device-side list overflowed (result undefined) */
+  RS_ERR_UNSUPPORTED = 9,    /* a valid request this build does not handle (key_size > 16) */
+  RS_ERR_INTERNAL = 10       /* a device-side consistency check failed (result undefined) */
+} rs_status;
+
+/*
+ * Sort n records in place.
+ *   in        device pointer, n * rec_size bytes, 16-byte aligned: the records; on
+ *             completion they are in key order (section 1: the sorted sequence).
+ *   tmp       device pointer, n * rec_size bytes, 16-byte aligned, not overlapping `in`:
+ *             scratch (the other buffer of every distribution pass); contents undefined after.
+ *   n         number of records (n <= 1: nothing is launched).
+ *   rec_size  bytes per record: a multiple of 8, 8..256.
+ *   key_size  key bytes: 1..16, <= rec_size.
+ *   stream    CUDA stream for all work.
+ */
+rs_status radix_sort(void *in, void *tmp, uint64_t n, uint32_t rec_size, uint32_t key_size,
+                     rs_stream_t stream);
+
+/*
+ * Sort many independent instances in one call: segment s is records
+ * [seg_offsets[s], seg_offsets[s+1]) of `in`, sorted on its own, in place.
+ *   seg_offsets  DEVICE pointer to n_segs + 1 uint64 values: non-decreasing, [0] = 0,
+ *                [n_segs] = total records (not checked on the host; violating it is
+ *                undefined behaviour).
+ *   n_segs       number of segments (0: nothing is launched).
+ *   total        seg_offsets[n_segs], passed by the caller so no device read is needed.
+ *   in, tmp, rec_size, key_size, stream: as for radix_sort, with n = total.
+ */
+rs_status radix_sort_segmented(void *in, void *tmp, const uint64_t *seg_offsets, uint64_t n_segs,
+                               uint64_t total, uint32_t rec_size, uint32_t key_size,
+                               rs_stream_t stream);
+
+/*
+ * One stable counting-sort phase (section 1) on one digit: the records of `src` are written
+ * to `dst` ordered by key bits [bit_lo, bit_lo + width), ties in input order.  This is the
+ * distribution pass that every level of the sort makes on each large bin (section 3.1, step 1).
+ *   src, dst   device pointers, n * rec_size bytes each, 16-byte aligned, not overlapping.
+ *   width      1..10; bit_lo + width <= 8 * key_size.
+ */
+rs_status radix_partition(const void *src, void *dst, uint64_t n, uint32_t rec_size, uint32_t key_size,
+                          uint32_t bit_lo, uint32_t width, rs_stream_t stream);
+
+/*
+ * Histogram of one digit (the counting step of a phase, section 1):
+ * counts[v] = number of records whose key bits [bit_lo, bit_lo + width) equal v.
+ *   counts   DEVICE pointer to 2^width uint64 values (written, not accumulated).
+ *   width    1..10; bit_lo + width <= 8 * key_size.
+ */
+rs_status radix_histogram(const void *src, uint64_t n, uint32_t rec_size, uint32_t key_size, uint32_t bit_lo,
+                          uint32_t width, uint64_t *counts, rs_stream_t stream);
+
+/*
+ * Waits for `stream` to drain, then reports (and clears) the device-side status of the
+ * calls made on it: RS_OK, RS_ERR_DEVICE_TIMEOUT, RS_ERR_QUEUE_OVERFLOW, RS_ERR_INTERNAL
+ * (a destination or range check failed; the offending writes were skipped), or RS_ERR_CUDA.
+ */
+rs_status radix_sort_status(rs_stream_t stream);
+
+/* Human-readable name of a status code (static storage). */
+const char *radix_sort_strerror(rs_status status);
+
+/* Frees every library-owned workspace (after synchronising the device). */
+rs_status radix_sort_release(void);
+
+/*
+ * Tuning knobs (process-wide; a zero field means "automatic").  They change speed only,
+ * never the result.
+ */
+typedef struct rs_plan {
+  uint32_t digit_bits_max;  /* widest digit of a distribution pass: 8..10 */
+  uint32_t tile_records;    /* records per scatter tile: 512..4096, a multiple of 512 */
+  uint32_t chunk_records;   /* largest bin sorted on chip: 64.. the shared-memory maximum */
+  uint32_t sm_limit;        /* use at most this many SMs for the persistent grids */
+  uint32_t watchdog_polls;  /* polls of a look-back wait before it gives up */
+} rs_plan;
+
+rs_status radix_sort_set_plan(const rs_plan *plan);
+rs_status radix_sort_get_plan(rs_plan *plan);
+
+/* Kernels launched by this process through the library so far (all entry points). */
+uint64_t radix_sort_launch_count(void);
+
+/*
+ * Per-launch timing (for benchmarks).  radix_sort_profile(1) starts a session: every kernel
+ * the library launches from then on is bracketed by two CUDA events recorded on the
+ * launching stream; radix_sort_profile(0) stops recording.  radix_sort_profile_read() waits
+ * for the recorded events and writes up to `max` records (kernel id, level, milliseconds)
+ * in launch order; it returns how many it wrote (out = NULL: how many there are), or -1 on
+ * a CUDA error.  Kernel ids: RS_K_*.
+ */
+enum {
+  RS_K_INIT = 0,      /* set-up of the control block, first bin list or chunk */
+  RS_K_HIST = 1,      /* histogram of a level's digit (+ bucket bases) */
+  RS_K_HIST_REDO = 2, /* level-0 recount when the first digit had to move */
+  RS_K_SCATTER = 3,   /* stable distribution of a level's bins (the dominant kernel) */
+  RS_K_CLASSIFY = 4,  /* sub-bin classification and the next level's bin list */
+  RS_K_CHUNK = 5,     /* on-chip sorts of small bins */
+  RS_K_COPY = 6       /* copy-back of finished ranges left in tmp */
+};
+typedef struct rs_kernel_time {
+  uint32_t kernel;
+  uint32_t level;
+  float ms;
+} rs_kernel_time;
+
+rs_status radix_sort_profile(int enable);
+int64_t radix_sort_profile_read(rs_kernel_time *out, int64_t max);
+
+/*
+ * Testing only.  flags = 1: in the next call, the first look-back wait of each distribution
+ * pass waits on a device word that nothing writes, so the bounded wait must give up:
+ * the call completes, its result is undefined, and radix_sort_status() reports
+ * RS_ERR_DEVICE_TIMEOUT.  The flag applies to one call.  flags = 0 clears it.
+ */
+rs_status radix_sort_test_inject(uint32_t flags);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* RADIX_GB300_H */

@@ -1,0 +1,184 @@
+"""GB300-native MSD radix sorting of fixed-size records.
+
+The method is RADULS2 (Kokot, Deorowicz, Dlugosz, "Even faster sorting of (not only)
+integers"): an MSD radix sort that distributes records by key digits and sorts small bins
+on chip.  Everything runs in the CUDA library ``libradix_gb300.so`` (C ABI in
+``include/radix_gb300.h``); this module only marshals arguments.  PyTorch provides device
+memory and streams.
+
+Records are rows of a contiguous tensor: a 2-D tensor of shape (n, k) holds n records of
+k * element_size bytes; a 1-D 8-byte tensor holds n records of 8 bytes.  The key is the
+first ``key_size`` bytes of a record, read as a little-endian unsigned integer.
+"""
+from __future__ import annotations
+
+import ctypes
+
+from ._lib import KERNEL_NAMES, RadixSortError, RsKernelTime, RsPlan, check, lib
+
+__all__ = ["sort", "sort_host", "sort_segmented", "partition", "histogram", "status", "release", "set_plan",
+           "get_plan", "launch_count", "profile", "RadixSortError", "lib"]
+
+
+def _torch():
+    import torch
+    return torch
+
+
+def _rec_size(t) -> int:
+    if t.dim() == 1:
+        return t.element_size()
+    if t.dim() != 2:
+        raise ValueError("records must be a 1-D or 2-D tensor")
+    return t.shape[1] * t.element_size()
+
+
+def _stream(stream):
+    torch = _torch()
+    s = torch.cuda.current_stream() if stream is None else stream
+    return ctypes.c_void_p(s.cuda_stream)
+
+
+def _need_cuda(t, what):
+    if not t.is_cuda or not t.is_contiguous():
+        raise ValueError(f"{what} must be a contiguous CUDA tensor")
+
+
+def sort(records, key_size: int, tmp=None, stream=None):
+    """Sort records by key (stable), in place; returns ``records``.
+
+    CUDA tensor: sorted on its device, asynchronously on ``stream`` (default: the current
+    stream).  CPU tensor: copied to the current CUDA device, sorted there, and copied back
+    (synchronously); pinned memory makes the copies faster.
+    ``tmp``: optional scratch of the same size on the same device.
+    """
+    torch = _torch()
+    if records.device.type == "cpu":
+        dev = torch.empty_like(records, device="cuda")
+        dev.copy_(records, non_blocking=True)
+        sort(dev, key_size, tmp=tmp, stream=stream)
+        records.copy_(dev, non_blocking=False)
+        return records
+    _need_cuda(records, "records")
+    n = records.shape[0]
+    if tmp is None:
+        tmp = torch.empty_like(records)
+    _need_cuda(tmp, "tmp")
+    check(lib().radix_sort(records.data_ptr(), tmp.data_ptr(), n, _rec_size(records), key_size, _stream(stream)),
+          "radix_sort")
+    return records
+
+
+def sort_host(h_in, key_size: int, h_out=None, d_buf=None, d_tmp=None, stream=None):
+    """Sort host records through the GPU: copy ``h_in`` to the device, sort, copy back.
+
+    The result goes to ``h_out`` (default: ``h_in`` itself).  ``d_buf``/``d_tmp``: optional
+    device buffers of the same shape, reused across calls.  Pinned host tensors make the
+    copies asynchronous.  Returns after the result is on the host.
+    """
+    torch = _torch()
+    if d_buf is None:
+        d_buf = torch.empty_like(h_in, device="cuda")
+    if d_tmp is None:
+        d_tmp = torch.empty_like(d_buf)
+    s = torch.cuda.current_stream() if stream is None else stream
+    with torch.cuda.stream(s):
+        d_buf.copy_(h_in, non_blocking=True)
+        sort(d_buf, key_size, tmp=d_tmp, stream=s)
+        out = h_in if h_out is None else h_out
+        out.copy_(d_buf, non_blocking=True)
+    s.synchronize()
+    return out
+
+
+def sort_segmented(records, offsets, key_size: int, tmp=None, stream=None, total: int | None = None):
+    """Sort each segment [offsets[s], offsets[s+1]) of ``records`` on its own, in place.
+
+    ``offsets``: CUDA int64/uint64 tensor of n_segs + 1 non-decreasing record offsets,
+    offsets[0] = 0, offsets[-1] = number of records.  ``total`` (= offsets[-1]) avoids a
+    device read when given.
+    """
+    torch = _torch()
+    _need_cuda(records, "records")
+    _need_cuda(offsets, "offsets")
+    if offsets.element_size() != 8:
+        raise ValueError("offsets must be 64-bit")
+    n_segs = offsets.numel() - 1
+    if total is None:
+        total = int(offsets[-1].item()) if n_segs >= 0 else 0
+    if tmp is None:
+        tmp = torch.empty_like(records)
+    check(lib().radix_sort_segmented(records.data_ptr(), tmp.data_ptr(), offsets.data_ptr(), max(n_segs, 0), total,
+                                     _rec_size(records), key_size, _stream(stream)), "radix_sort_segmented")
+    return records
+
+
+def partition(src, dst, key_size: int, bit_lo: int, width: int, stream=None):
+    """One stable counting-sort pass: ``dst`` = ``src`` ordered by key bits [bit_lo, bit_lo+width)."""
+    _need_cuda(src, "src")
+    _need_cuda(dst, "dst")
+    check(lib().radix_partition(src.data_ptr(), dst.data_ptr(), src.shape[0], _rec_size(src), key_size, bit_lo, width,
+                                _stream(stream)), "radix_partition")
+    return dst
+
+
+def histogram(src, key_size: int, bit_lo: int, width: int, stream=None):
+    """Counts of key bits [bit_lo, bit_lo+width) over the records (CUDA int64 tensor, 2^width)."""
+    torch = _torch()
+    _need_cuda(src, "src")
+    out = torch.empty(1 << width, dtype=torch.int64, device=src.device)
+    check(lib().radix_histogram(src.data_ptr(), src.shape[0], _rec_size(src), key_size, bit_lo, width, out.data_ptr(),
+                                _stream(stream)), "radix_histogram")
+    return out
+
+
+def status(stream=None) -> int:
+    """Drains the stream and returns the device-side status code of its calls (0 = ok)."""
+    return lib().radix_sort_status(_stream(stream))
+
+
+def check_status(stream=None) -> None:
+    check(status(stream), "device status")
+
+
+def release() -> None:
+    check(lib().radix_sort_release(), "radix_sort_release")
+
+
+def set_plan(digit_bits_max=0, tile_records=0, chunk_records=0, sm_limit=0, watchdog_polls=0) -> None:
+    p = RsPlan(digit_bits_max, tile_records, chunk_records, sm_limit, watchdog_polls)
+    check(lib().radix_sort_set_plan(ctypes.byref(p)), "radix_sort_set_plan")
+
+
+def get_plan() -> dict:
+    p = RsPlan()
+    check(lib().radix_sort_get_plan(ctypes.byref(p)), "radix_sort_get_plan")
+    return {f: getattr(p, f) for f, _ in RsPlan._fields_}
+
+
+def launch_count() -> int:
+    return int(lib().radix_sort_launch_count())
+
+
+class profile:
+    """Context manager: per-kernel CUDA-event timings of the library's launches.
+
+    ``with profile() as p: ...`` then ``p.records`` = [(kernel_name, level, ms), ...].
+    """
+
+    def __enter__(self):
+        check(lib().radix_sort_profile(1), "radix_sort_profile")
+        self.records = []
+        return self
+
+    def __exit__(self, *exc):
+        L = lib()
+        L.radix_sort_profile(0)
+        n = L.radix_sort_profile_read(None, 0)
+        buf = (RsKernelTime * max(1, n))()
+        got = L.radix_sort_profile_read(buf, n)
+        if got < 0:
+            raise RadixSortError(6, "radix_sort_profile_read")
+        self.records = [(KERNEL_NAMES.get(buf[i].kernel, str(buf[i].kernel)), buf[i].level, buf[i].ms)
+                        for i in range(got)]
+        return False

@@ -1,0 +1,491 @@
+// C ABI of the sorter: argument validation, the per-(device, stream) workspace, and the
+// host driver that launches the levels of the MSD radix sort (Kokot et al., section 3.1).
+//
+// The driver never reads device memory: it launches a fixed sequence of kernels per level
+// and every kernel reads the amount of work left for it from the device control block,
+// returning at once when there is none.  A level uses a digit of at least kWMin bits that
+// starts at the bin's highest differing key bit, so a key of key_size bytes needs at most
+// key_size levels.
+#include <atomic>
+#include <cstdio>
+#include <cstring>
+#include <map>
+#include <mutex>
+#include <utility>
+#include <vector>
+
+#include "radix_gb300.h"
+#include "rs_internal.cuh"
+
+namespace rsg {
+
+u32 chunk_capacity(u32 RW);
+
+struct Workspace {
+  void* mem = nullptr;
+  size_t bytes = 0;
+  Ctl* ctl = nullptr;
+};
+
+static std::mutex g_mu;
+static std::map<std::pair<int, cudaStream_t>, Workspace> g_ws;
+static rs_plan g_plan = {0, 0, 0, 0, 0};
+static std::atomic<unsigned long long> g_launches{0};
+static std::map<int, int> g_sms;
+static std::atomic<unsigned> g_inject{0};
+
+static int sm_count(int dev) {
+  auto it = g_sms.find(dev);
+  if (it != g_sms.end()) return it->second;
+  int n = 0;
+  if (cudaDeviceGetAttribute(&n, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess || n <= 0) n = 1;
+  g_sms[dev] = n;
+  return n;
+}
+
+// Sizes of every workspace region for a job.
+struct Caps {
+  u64 bins, base, mslots, status, chunks, pieces;
+  size_t bytes;
+  size_t off_ctl, off_bins0, off_bins1, off_base0, off_base1, off_masks, off_status, off_chunks, off_pieces;
+};
+
+static size_t al(size_t x) { return (x + 255) & ~(size_t)255; }
+
+static Caps caps_for(u64 n, u32 T, u32 cm, u32 wmax, u32 KW, bool wide, u64 n_segs) {
+  Caps c;
+  c.bins = n / ((u64)cm + 1) + 2;
+  c.base = 256ull * c.bins + 2 * (n / cm) + (1ull << wmax) + 64;
+  c.mslots = n / ((u64)cm + 1) + 2;
+  c.status = (n / T + c.bins) * (1ull << wmax) + 64;
+  c.chunks = 6 * (n / cm) + n_segs + 16;
+  c.pieces = n / kPieceRecords + n / ((u64)cm + 1) + 16;
+  size_t o = 0;
+  c.off_ctl = o; o = al(o + sizeof(Ctl));
+  c.off_bins0 = o; o = al(o + c.bins * sizeof(Bin));
+  c.off_bins1 = o; o = al(o + c.bins * sizeof(Bin));
+  c.off_base0 = o; o = al(o + c.base * 8);
+  c.off_base1 = o; o = al(o + c.base * 8);
+  c.off_masks = o; o = al(o + c.mslots * 2 * KW * 8);
+  c.off_status = o; o = al(o + c.status * (wide ? 8 : 4));
+  c.off_chunks = o; o = al(o + c.chunks * sizeof(Chunk));
+  c.off_pieces = o; o = al(o + c.pieces * sizeof(Piece));
+  c.bytes = o;
+  return c;
+}
+
+static rs_status get_workspace(int dev, cudaStream_t s, size_t bytes, Workspace** out) {
+  std::lock_guard<std::mutex> lk(g_mu);
+  Workspace& w = g_ws[std::make_pair(dev, s)];
+  if (w.bytes < bytes) {
+    u32 err_keep = 0;
+    if (w.mem) {
+      // keep the sticky error bits of earlier calls on this stream
+      if (cudaStreamSynchronize(s) != cudaSuccess) return RS_ERR_CUDA;
+      cudaMemcpy(&err_keep, &w.ctl->err, sizeof(u32), cudaMemcpyDeviceToHost);
+      cudaFree(w.mem);
+      w.mem = nullptr;
+      w.bytes = 0;
+    }
+    size_t want = bytes + bytes / 4;  // head room so that slightly larger calls reuse it
+    void* m = nullptr;
+    if (cudaMalloc(&m, want) != cudaSuccess) {
+      cudaGetLastError();
+      want = bytes;
+      if (cudaMalloc(&m, want) != cudaSuccess) {
+        cudaGetLastError();
+        return RS_ERR_NO_MEMORY;
+      }
+    }
+    if (cudaMemset(m, 0, sizeof(Ctl)) != cudaSuccess) return RS_ERR_CUDA;
+    w.mem = m;
+    w.bytes = want;
+    w.ctl = (Ctl*)m;
+    if (err_keep) cudaMemcpy(&w.ctl->err, &err_keep, sizeof(u32), cudaMemcpyHostToDevice);
+  }
+  *out = &w;
+  return RS_OK;
+}
+
+struct Setup {
+  Job j;
+  Caps c;
+  int dev;
+  int sms;
+};
+
+static rs_status validate_layout(uint32_t rec_size, uint32_t key_size) {
+  if (rec_size == 0 || rec_size % 8 != 0 || rec_size > 256) return RS_ERR_INVALID_ARG;
+  if (key_size == 0 || key_size > rec_size) return RS_ERR_INVALID_ARG;
+  if (key_size > 16) return RS_ERR_UNSUPPORTED;
+  return RS_OK;
+}
+
+static bool overlap(const void* a, const void* b, u64 bytes) {
+  const uintptr_t x = (uintptr_t)a, y = (uintptr_t)b;
+  return x < y + bytes && y < x + bytes;
+}
+
+static rs_status validate_buffers(const void* a, const void* b, u64 n, uint32_t rec_size) {
+  if (n > UINT64_MAX / rec_size) return RS_ERR_TOO_LARGE;
+  const u64 bytes = n * rec_size;
+  if (bytes > (u64)UINTPTR_MAX / 2) return RS_ERR_TOO_LARGE;
+  if (!a || !b) return RS_ERR_INVALID_ARG;
+  if ((((uintptr_t)a) | ((uintptr_t)b)) & 15) return RS_ERR_MISALIGNED;
+  if (overlap(a, b, bytes)) return RS_ERR_OVERLAP;
+  return RS_OK;
+}
+
+static rs_status check_device_ptr(const void* p) {
+  cudaPointerAttributes at;
+  if (cudaPointerGetAttributes(&at, p) != cudaSuccess) {
+    cudaGetLastError();
+    return RS_ERR_INVALID_ARG;
+  }
+  if (at.type != cudaMemoryTypeDevice && at.type != cudaMemoryTypeManaged) return RS_ERR_INVALID_ARG;
+  return RS_OK;
+}
+
+static rs_status setup_job(void* in, void* tmp, u64 n, u32 rec_size, u32 key_size, u64 n_segs,
+                           cudaStream_t stream, Setup* st) {
+  if (check_device_ptr(in) != RS_OK || check_device_ptr(tmp) != RS_OK) return RS_ERR_INVALID_ARG;
+  int dev = 0;
+  if (cudaGetDevice(&dev) != cudaSuccess) return RS_ERR_CUDA;
+  Job& j = st->j;
+  memset(&j, 0, sizeof j);
+  j.buf[0] = (u64*)in;
+  j.buf[1] = (u64*)tmp;
+  j.n = n;
+  j.RW = rec_size / 8;
+  j.K = key_size;
+  j.KW = key_size > 8 ? 2 : 1;
+  for (u32 w = 0; w < 2; w++) {
+    const int bytes = (int)key_size - 8 * (int)w;
+    j.keymask[w] = bytes >= 8 ? ~0ull : bytes <= 0 ? 0ull : ((1ull << (8 * bytes)) - 1);
+  }
+  rs_plan p;
+  {
+    std::lock_guard<std::mutex> lk(g_mu);
+    p = g_plan;
+  }
+  j.wmax = p.digit_bits_max ? p.digit_bits_max : 9;
+  u32 T = 4096;
+  while (T > 512 && (u64)T * rec_size > 65536) T >>= 1;
+  if (p.tile_records) T = p.tile_records;
+  j.T = T;
+  const u32 cap = chunk_capacity(j.RW);
+  j.chunk_max = p.chunk_records && p.chunk_records < cap ? p.chunk_records : cap;
+  j.watchdog = p.watchdog_polls ? p.watchdog_polls : (1u << 16);
+  j.inject = g_inject.exchange(0);
+  j.wide = n >= (1ull << 30) ? 1u : 0u;  // 64-bit look-back words for bins of 2^30 records or more
+  j.n_segs = n_segs;
+  Caps c = caps_for(n, j.T, j.chunk_max, j.wmax, j.KW, j.wide != 0, n_segs);
+  Workspace* w = nullptr;
+  rs_status r = get_workspace(dev, stream, c.bytes, &w);
+  if (r != RS_OK) return r;
+  char* base = (char*)w->mem;
+  j.ctl = (Ctl*)(base + c.off_ctl);
+  j.bins[0] = (Bin*)(base + c.off_bins0);
+  j.bins[1] = (Bin*)(base + c.off_bins1);
+  j.cap_bins = c.bins;
+  j.base[0] = (u64*)(base + c.off_base0);
+  j.base[1] = (u64*)(base + c.off_base1);
+  j.cap_base = c.base;
+  j.masks = (u64*)(base + c.off_masks);
+  j.cap_mslots = c.mslots;
+  j.status[0] = j.status[1] = base + c.off_status;
+  j.cap_status = c.status;
+  j.chunks = (Chunk*)(base + c.off_chunks);
+  j.cap_chunks = c.chunks;
+  j.pieces = (Piece*)(base + c.off_pieces);
+  j.cap_pieces = c.pieces;
+  st->c = c;
+  st->dev = dev;
+  int sms = sm_count(dev);
+  if (p.sm_limit && (int)p.sm_limit < sms) sms = (int)p.sm_limit;
+  st->sms = sms;
+  return RS_OK;
+}
+
+static void count(int k) {
+  if (k > 0) g_launches += (unsigned long long)k;
+}
+
+// Optional per-launch timing: CUDA events recorded on the launching stream around each
+// kernel of the sort (enabled by radix_sort_profile).
+struct ProfRec {
+  cudaEvent_t a, b;
+  u32 kernel, level;
+};
+static std::mutex g_prof_mu;
+static bool g_prof_on = false;
+static std::vector<ProfRec> g_prof;     // records of this profiling session
+static std::vector<cudaEvent_t> g_evpool;
+static size_t g_evnext = 0;
+
+static cudaEvent_t prof_event() {
+  if (g_evnext == g_evpool.size()) {
+    cudaEvent_t e;
+    if (cudaEventCreate(&e) != cudaSuccess) return nullptr;
+    g_evpool.push_back(e);
+  }
+  return g_evpool[g_evnext++];
+}
+
+template <typename F>
+static int timed(u32 kernel, u32 level, cudaStream_t s, F&& launch) {
+  ProfRec r = {nullptr, nullptr, kernel, level};
+  bool on;
+  {
+    std::lock_guard<std::mutex> lk(g_prof_mu);
+    on = g_prof_on;
+    if (on) {
+      r.a = prof_event();
+      r.b = prof_event();
+      on = r.a && r.b;
+    }
+  }
+  if (on) cudaEventRecord(r.a, s);
+  const int k = launch();
+  if (on) {
+    cudaEventRecord(r.b, s);
+    std::lock_guard<std::mutex> lk(g_prof_mu);
+    g_prof.push_back(r);
+  }
+  count(k);
+  return k;
+}
+
+// Levels 0..K-1 of distribution passes, then the on-chip sorts and the copy-back.
+static rs_status run_levels(const Setup& st, cudaStream_t s) {
+  const Job& j = st.j;
+  const u32 gh = (u32)st.sms * (u32)hist_ctas_per_sm(j);
+  const u32 gs = (u32)st.sms * (u32)scatter_ctas_per_sm(j, j.wide != 0);
+  const u32 gc = (u32)st.sms * 2;
+  const int levels = (int)j.K;  // each level consumes >= 8 key bits
+  for (int lv = 0; lv < levels; lv++) {
+    if (timed(RS_K_HIST, lv, s, [&] { return launch_hist(j, lv, 0, gh, s); }) < 0) return RS_ERR_CUDA;
+    if (lv == 0 && timed(RS_K_HIST_REDO, lv, s, [&] { return launch_hist(j, 0, 1, gh, s); }) < 0) return RS_ERR_CUDA;
+    if (timed(RS_K_SCATTER, lv, s, [&] { return launch_scatter(j, lv, j.wide != 0, gs, s); }) < 0) return RS_ERR_CUDA;
+    if (timed(RS_K_CLASSIFY, lv, s, [&] { return launch_classify(j, lv, gc, s); }) < 0) return RS_ERR_CUDA;
+  }
+  const u32 gch = (u32)st.sms * (u32)chunk_ctas_per_sm(j);
+  if (timed(RS_K_CHUNK, levels, s, [&] { return launch_chunks(j, gch, s); }) < 0) return RS_ERR_CUDA;
+  if (timed(RS_K_COPY, levels, s, [&] { return launch_copy(j, (u32)st.sms * 2, s); }) < 0) return RS_ERR_CUDA;
+  return RS_OK;
+}
+
+}  // namespace rsg
+
+using namespace rsg;
+
+extern "C" {
+
+rs_status radix_sort(void* in, void* tmp, uint64_t n, uint32_t rec_size, uint32_t key_size, rs_stream_t stream) {
+  rs_status r = validate_layout(rec_size, key_size);
+  if (r != RS_OK) return r;
+  if (n > UINT64_MAX / rec_size) return RS_ERR_TOO_LARGE;
+  if (n <= 1) return RS_OK;
+  if ((r = validate_buffers(in, tmp, n, rec_size)) != RS_OK) return r;
+  cudaStream_t s = (cudaStream_t)stream;
+  Setup st;
+  if ((r = setup_job(in, tmp, n, rec_size, key_size, 0, s, &st)) != RS_OK) return r;
+  const Job& j = st.j;
+  if (n <= j.chunk_max) {
+    if (timed(RS_K_INIT, 0, s, [&] { return launch_init_single_chunk(j, s); }) < 0) return RS_ERR_CUDA;
+    if (timed(RS_K_CHUNK, 0, s, [&] { return launch_chunks(j, 1, s); }) < 0) return RS_ERR_CUDA;
+    return RS_OK;
+  }
+  u32 lo, W;
+  plan_digit(n, 8 * key_size, j.chunk_max, j.wmax, &lo, &W);
+  if (timed(RS_K_INIT, 0, s, [&] { return launch_init_plain(j, lo, W, s); }) < 0) return RS_ERR_CUDA;
+  return run_levels(st, s);
+}
+
+rs_status radix_sort_segmented(void* in, void* tmp, const uint64_t* seg_offsets, uint64_t n_segs, uint64_t total,
+                               uint32_t rec_size, uint32_t key_size, rs_stream_t stream) {
+  rs_status r = validate_layout(rec_size, key_size);
+  if (r != RS_OK) return r;
+  if (total > UINT64_MAX / rec_size) return RS_ERR_TOO_LARGE;
+  if (n_segs == 0 || total <= 1) return RS_OK;
+  if (!seg_offsets) return RS_ERR_INVALID_ARG;
+  if ((r = validate_buffers(in, tmp, total, rec_size)) != RS_OK) return r;
+  if (check_device_ptr(seg_offsets) != RS_OK) return RS_ERR_INVALID_ARG;
+  cudaStream_t s = (cudaStream_t)stream;
+  Setup st;
+  if ((r = setup_job(in, tmp, total, rec_size, key_size, n_segs, s, &st)) != RS_OK) return r;
+  st.j.seg_off = (const u64*)seg_offsets;
+  if (timed(RS_K_INIT, 0, s, [&] { return launch_init_segments(st.j, (u32)st.sms * 4, s); }) < 0) return RS_ERR_CUDA;
+  return run_levels(st, s);
+}
+
+static rs_status one_pass(const void* src, void* dst, uint64_t n, uint32_t rec_size, uint32_t key_size,
+                          uint32_t bit_lo, uint32_t width, uint64_t* counts, rs_stream_t stream) {
+  rs_status r = validate_layout(rec_size, key_size);
+  if (r != RS_OK) return r;
+  if (width == 0 || width > (uint32_t)kWMax || bit_lo + width > 8 * key_size) return RS_ERR_INVALID_ARG;
+  if (n > UINT64_MAX / rec_size) return RS_ERR_TOO_LARGE;
+  cudaStream_t s = (cudaStream_t)stream;
+  if (counts) {  // histogram
+    if (n == 0) {
+      if (cudaMemsetAsync(counts, 0, sizeof(uint64_t) << width, s) != cudaSuccess) return RS_ERR_CUDA;
+      return RS_OK;
+    }
+    if (!src) return RS_ERR_INVALID_ARG;
+    if (((uintptr_t)src) & 15) return RS_ERR_MISALIGNED;
+  } else {
+    if (n == 0) return RS_OK;
+    if ((r = validate_buffers(src, dst, n, rec_size)) != RS_OK) return r;
+    if (n == 1) {
+      if (cudaMemcpyAsync(dst, src, rec_size, cudaMemcpyDeviceToDevice, s) != cudaSuccess) return RS_ERR_CUDA;
+      return RS_OK;
+    }
+  }
+  Setup st;
+  // the histogram has no destination: point the second buffer at the source (never written)
+  if ((r = setup_job(const_cast<void*>(src), counts ? const_cast<void*>(src) : dst, n, rec_size, key_size, 0, s, &st)) != RS_OK)
+    return r;
+  Job& j = st.j;
+  j.wmax = kWMax;  // the requested width, whatever the plan says
+  const u32 gh = (u32)st.sms * (u32)hist_ctas_per_sm(j);
+  int k;
+  if ((k = launch_init_plain(j, bit_lo, width, s)) < 0) return RS_ERR_CUDA;
+  count(k);
+  if (counts) {
+    if ((k = launch_hist(j, 0, 2, gh, s)) < 0) return RS_ERR_CUDA;
+    count(k);
+    if ((k = launch_read_counts(j, (u64*)counts, width, s)) < 0) return RS_ERR_CUDA;
+    count(k);
+    return RS_OK;
+  }
+  if ((k = launch_hist(j, 0, 3, gh, s)) < 0) return RS_ERR_CUDA;
+  count(k);
+  if ((k = launch_scatter(j, 0, j.wide != 0, (u32)st.sms * (u32)scatter_ctas_per_sm(j, j.wide != 0), s)) < 0)
+    return RS_ERR_CUDA;
+  count(k);
+  return RS_OK;
+}
+
+rs_status radix_partition(const void* src, void* dst, uint64_t n, uint32_t rec_size, uint32_t key_size,
+                          uint32_t bit_lo, uint32_t width, rs_stream_t stream) {
+  return one_pass(src, dst, n, rec_size, key_size, bit_lo, width, nullptr, stream);
+}
+
+rs_status radix_histogram(const void* src, uint64_t n, uint32_t rec_size, uint32_t key_size, uint32_t bit_lo,
+                          uint32_t width, uint64_t* counts, rs_stream_t stream) {
+  if (!counts) return RS_ERR_INVALID_ARG;
+  return one_pass(src, nullptr, n, rec_size, key_size, bit_lo, width, counts, stream);
+}
+
+rs_status radix_sort_status(rs_stream_t stream) {
+  cudaStream_t s = (cudaStream_t)stream;
+  if (cudaStreamSynchronize(s) != cudaSuccess) {
+    cudaGetLastError();
+    return RS_ERR_CUDA;
+  }
+  int dev = 0;
+  if (cudaGetDevice(&dev) != cudaSuccess) return RS_ERR_CUDA;
+  Ctl* ctl = nullptr;
+  {
+    std::lock_guard<std::mutex> lk(g_mu);
+    auto it = g_ws.find(std::make_pair(dev, s));
+    if (it == g_ws.end() || !it->second.mem) return RS_OK;
+    ctl = it->second.ctl;
+  }
+  u32 err = 0;
+  if (cudaMemcpy(&err, &ctl->err, sizeof err, cudaMemcpyDeviceToHost) != cudaSuccess) return RS_ERR_CUDA;
+  if (err) {
+    u32 zero = 0;
+    cudaMemcpy(&ctl->err, &zero, sizeof zero, cudaMemcpyHostToDevice);
+  }
+  if (err & kErrTimeout) return RS_ERR_DEVICE_TIMEOUT;
+  if (err & kErrOverflow) return RS_ERR_QUEUE_OVERFLOW;
+  if (err) return RS_ERR_INTERNAL;
+  return RS_OK;
+}
+
+const char* radix_sort_strerror(rs_status s) {
+  switch (s) {
+    case RS_OK: return "ok";
+    case RS_ERR_INVALID_ARG: return "invalid argument";
+    case RS_ERR_MISALIGNED: return "record buffer not 16-byte aligned";
+    case RS_ERR_OVERLAP: return "record buffers overlap";
+    case RS_ERR_TOO_LARGE: return "size too large";
+    case RS_ERR_NO_MEMORY: return "workspace allocation failed";
+    case RS_ERR_CUDA: return "CUDA error";
+    case RS_ERR_DEVICE_TIMEOUT: return "device-side wait hit its limit";
+    case RS_ERR_QUEUE_OVERFLOW: return "device-side list overflowed";
+    case RS_ERR_UNSUPPORTED: return "unsupported (key_size > 16)";
+    case RS_ERR_INTERNAL: return "device-side consistency check failed";
+  }
+  return "unknown status";
+}
+
+rs_status radix_sort_release(void) {
+  std::lock_guard<std::mutex> lk(g_mu);
+  if (g_ws.empty()) return RS_OK;
+  if (cudaDeviceSynchronize() != cudaSuccess) {
+    cudaGetLastError();
+  }
+  rs_status r = RS_OK;
+  for (auto& kv : g_ws)
+    if (kv.second.mem && cudaFree(kv.second.mem) != cudaSuccess) r = RS_ERR_CUDA;
+  g_ws.clear();
+  return r;
+}
+
+rs_status radix_sort_set_plan(const rs_plan* plan) {
+  if (!plan) return RS_ERR_INVALID_ARG;
+  rs_plan p = *plan;
+  if (p.digit_bits_max && (p.digit_bits_max < (u32)kWMin || p.digit_bits_max > (u32)kWMax)) return RS_ERR_INVALID_ARG;
+  if (p.tile_records && (p.tile_records < 512 || p.tile_records > 4096 || p.tile_records % 512)) return RS_ERR_INVALID_ARG;
+  if (p.chunk_records && p.chunk_records < 64) return RS_ERR_INVALID_ARG;
+  std::lock_guard<std::mutex> lk(g_mu);
+  g_plan = p;
+  return RS_OK;
+}
+
+rs_status radix_sort_get_plan(rs_plan* plan) {
+  if (!plan) return RS_ERR_INVALID_ARG;
+  std::lock_guard<std::mutex> lk(g_mu);
+  *plan = g_plan;
+  return RS_OK;
+}
+
+uint64_t radix_sort_launch_count(void) { return (uint64_t)g_launches.load(); }
+
+rs_status radix_sort_profile(int enable) {
+  std::lock_guard<std::mutex> lk(g_prof_mu);
+  if (enable) {
+    g_prof.clear();
+    g_evnext = 0;
+  }
+  g_prof_on = enable != 0;
+  return RS_OK;
+}
+
+int64_t radix_sort_profile_read(rs_kernel_time* out, int64_t max) {
+  std::lock_guard<std::mutex> lk(g_prof_mu);
+  int64_t k = 0;
+  for (const ProfRec& r : g_prof) {
+    if (k >= max || !out) break;
+    float ms = 0.f;
+    if (cudaEventSynchronize(r.b) != cudaSuccess || cudaEventElapsedTime(&ms, r.a, r.b) != cudaSuccess) {
+      cudaGetLastError();
+      return -1;
+    }
+    out[k].kernel = r.kernel;
+    out[k].level = r.level;
+    out[k].ms = ms;
+    k++;
+  }
+  return out ? k : (int64_t)g_prof.size();
+}
+
+rs_status radix_sort_test_inject(uint32_t flags) {
+  if (flags > 1) return RS_ERR_INVALID_ARG;
+  g_inject = flags;
+  return RS_OK;
+}
+
+}  // extern "C"

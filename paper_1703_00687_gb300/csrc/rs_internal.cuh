@@ -1,0 +1,366 @@
+// Internal declarations shared by the sorter's CUDA translation units.
+//
+// The method is the MSD radix sort of Kokot, Deorowicz and Dlugosz ("Even faster sorting
+// of (not only) integers", section 3.1): distribute the records of a bin by a digit of the
+// key into sub-bins (a stable counting sort: histogram, exclusive prefix sum, scatter),
+// recurse into every sub-bin independently, and switch to an on-chip sorter once a bin is
+// small.  Here a "bin" is a contiguous range of records; a level is one distribution pass
+// over every large bin at once.
+//
+// Record layout: rec_size bytes = RW 8-byte words.  The key is bytes [0, key_size) read as
+// a little-endian unsigned integer: key bit b is bit (b mod 64) of word floor(b / 64), so
+// word 1 (bytes 8..15) is more significant than word 0.  Only key_size <= 16 is supported
+// (the paper's keys are 8 and 16 bytes, section 3.3).
+#pragma once
+#include <cstdint>
+#include <cuda_runtime.h>
+
+namespace rsg {
+
+using u64 = unsigned long long;
+using u32 = unsigned int;
+using u16 = unsigned short;
+using u8 = unsigned char;
+
+constexpr int kThreads = 512;                 // threads of every sorting CTA
+constexpr int kWarps = kThreads / 32;
+constexpr int kWMax = 10;                     // widest digit (bits) a distribution pass supports
+constexpr int kWMin = 8;                      // narrowest digit of a pass that has 8 key bits to use
+constexpr u32 kFull = 0xffffffffu;
+
+// device error bits (reported by radix_sort_status)
+enum : u32 { kErrTimeout = 1u, kErrOverflow = 2u, kErrInternal = 4u };
+
+// Bin flags
+enum : u32 { kBinRedo = 1u, kBinEqual = 2u };
+
+// Chunk flags
+enum : u32 { kChSrcTmp = 1u, kChCopyOnly = 2u, kChSegmented = 4u };
+
+// A bin handled by a multi-CTA distribution pass.
+struct Bin {
+  u64 begin;        // first record
+  u64 size;         // records
+  u64 tile_start;   // number of the bin's first tile within its level
+  u64 base_off;     // first of its 2^W entries in the level's bucket-base pool
+  u64 status_off;   // first of its tiles * 2^W look-back words
+  u64 kand[2];      // AND / OR of the bin's keys (level 0 only: picks the first useful digit)
+  u64 kor[2];
+  u32 lo, W;        // the digit is key bits [lo, lo + W)
+  u32 parity;       // 0: the bin's records are in `in`; 1: in `tmp`
+  u32 flags;
+  u32 done;         // tiles counted by the histogram pass (finds the last CTA of the bin)
+  u32 pad;
+};
+
+// A contiguous range of records sorted completely by one CTA in shared memory.  It is one
+// small bin, or several consecutive small sub-bins of the same parent (they share every key
+// bit above the parent's digit and are already in digit order, so sorting the whole range
+// by key sorts each of them).
+struct Chunk {
+  u64 begin;
+  u32 size;
+  u32 flags;        // kChSrcTmp: records are in tmp (else in); kChCopyOnly: already sorted
+  u64 seg_first;    // segmented chunks: first segment (index into the offsets array)
+  u32 seg_count;
+  u32 pad;
+};
+
+// A range of finished records that lives in tmp and must be copied to in.
+struct Piece {
+  u64 begin, size;
+};
+
+// Control block in device memory.  Lists are double-buffered by level parity.
+struct Ctl {
+  u32 err, pad0;
+  u64 nbins[2];
+  u64 ntiles[2];
+  u64 base_used[2];
+  u64 status_used[2];
+  u64 s_ticket;     // tile dispenser of the scatter pass
+  u32 cls_done;     // classify CTAs finished (the last one finalises the next list)
+  u32 pad1;
+  u64 mslot_used;   // mask slots handed out this level
+  u64 nchunks, chunk_ticket;
+  u64 npieces, piece_ticket;
+  u32 never;        // stays 0: the word an injected stall waits on
+  u32 pad2;
+};
+
+// Everything a kernel needs about one call, passed by value.
+struct Job {
+  u64* buf[2];        // [0] = in, [1] = tmp
+  u64 n;              // records
+  u32 RW;             // words per record
+  u32 K;              // key bytes
+  u32 KW;             // key words (1 or 2)
+  u32 T;              // records per tile of a distribution pass
+  u32 chunk_max;      // largest range one CTA sorts on chip
+  u32 wmax;           // widest digit of a pass (<= kWMax)
+  u32 watchdog;       // look-back polls before giving up
+  u32 wide;           // look-back words are 64-bit (bins of 2^30 records or more)
+  u32 inject;         // testing: 1 = the first look-back wait of a pass waits on Ctl::never
+  u32 pad;
+  u64 keymask[2];     // key bits of words 0 and 1
+  Ctl* ctl;
+  Bin* bins[2];
+  u64 cap_bins;
+  u64* base[2];       // bucket counts, then (after the scan) bases | (mask slot + 1) << 40
+  u64 cap_base;
+  u64* masks;         // per mask slot: AND[KW], OR[KW]
+  u64 cap_mslots;
+  void* status[2];    // look-back words (u32 or u64)
+  u64 cap_status;
+  Chunk* chunks;
+  u64 cap_chunks;
+  Piece* pieces;
+  u64 cap_pieces;
+  const u64* seg_off; // segmented mode: n_segs + 1 record offsets
+  u64 n_segs;
+};
+
+constexpr u64 kBaseMask = (1ull << 40) - 1;   // bucket base (records)
+constexpr int kSlotShift = 40;                 // mask slot + 1 above it (0 = none)
+constexpr u64 kPieceRecords = 1ull << 16;      // copy-back granularity
+
+// ---------------------------------------------------------------------------- keys
+template <int KW>
+struct Key {
+  u64 w[KW];
+};
+
+template <int KW>
+__device__ __forceinline__ Key<KW> load_key(const u64* rec, const Job& j) {
+  Key<KW> k;
+#pragma unroll
+  for (int i = 0; i < KW; i++) k.w[i] = rec[i] & j.keymask[i];
+  return k;
+}
+
+// Digit = key bits [lo, lo + W), W <= 16.
+template <int KW>
+__device__ __forceinline__ u32 digit_of(const Key<KW>& k, u32 lo, u32 W) {
+  u64 v;
+  if (KW == 1) {
+    v = k.w[0] >> lo;
+  } else {
+    const u32 sh = lo & 63;
+    if (lo >= 64) {
+      v = k.w[KW - 1] >> sh;
+    } else {
+      v = k.w[0] >> sh;
+      if (sh != 0 && sh + W > 64) v |= k.w[KW - 1] << (64 - sh);
+    }
+  }
+  return (u32)v & ((1u << W) - 1u);
+}
+
+template <int KW>
+__device__ __forceinline__ bool key_less(const Key<KW>& a, const Key<KW>& b) {
+  if (KW == 2 && a.w[KW - 1] != b.w[KW - 1]) return a.w[KW - 1] < b.w[KW - 1];
+  return a.w[0] < b.w[0];
+}
+
+template <int KW>
+__device__ __forceinline__ bool key_eq(const Key<KW>& a, const Key<KW>& b) {
+  bool e = a.w[0] == b.w[0];
+  if (KW == 2) e = e && a.w[KW - 1] == b.w[KW - 1];
+  return e;
+}
+
+// Position of the highest set bit plus one (0 if none) over a KW-word value.
+__host__ __device__ inline u32 top_bit_plus1(u64 w0, u64 w1) {
+#ifdef __CUDA_ARCH__
+  if (w1) return 128u - (u32)__clzll((long long)w1);
+  if (w0) return 64u - (u32)__clzll((long long)w0);
+#else
+  if (w1) return 128u - (u32)__builtin_clzll(w1);
+  if (w0) return 64u - (u32)__builtin_clzll(w0);
+#endif
+  return 0;
+}
+
+// Digit plan for a bin of `size` records whose highest differing key bit is p - 1: enough
+// bits that an average sub-bin fits one on-chip sort, spread evenly over the passes still
+// needed, at least kWMin (bounds the number of levels) and at most wmax.
+__host__ __device__ inline void plan_digit(u64 size, u32 p, u32 chunk_max, u32 wmax, u32* lo, u32* W) {
+  u32 need = 0;
+  while (need < 63 && (size >> need) > chunk_max) need++;
+  u32 passes = (need + wmax - 1) / wmax;
+  if (passes == 0) passes = 1;
+  u32 w = (need + passes - 1) / passes;
+  if (w < (u32)kWMin) w = kWMin;
+  if (w > wmax) w = wmax;
+  if (w > p) w = p;
+  if (w == 0) w = 1;
+  *W = w;
+  *lo = p >= w ? p - w : 0;
+}
+
+__host__ __device__ inline u64 ceil_div(u64 a, u64 b) { return (a + b - 1) / b; }
+
+// ---------------------------------------------------------------------- warp helpers
+__device__ __forceinline__ u32 lanemask_lt() {
+  u32 m;
+  asm("mov.u32 %0, %%lanemask_lt;" : "=r"(m));
+  return m;
+}
+
+__device__ __forceinline__ u32 ld_acquire(const u32* p) {
+  u32 v;
+  asm volatile("ld.acquire.gpu.global.u32 %0, [%1];" : "=r"(v) : "l"(p) : "memory");
+  return v;
+}
+__device__ __forceinline__ u64 ld_acquire(const u64* p) {
+  u64 v;
+  asm volatile("ld.acquire.gpu.global.u64 %0, [%1];" : "=l"(v) : "l"(p) : "memory");
+  return v;
+}
+__device__ __forceinline__ void st_release(u32* p, u32 v) {
+  asm volatile("st.release.gpu.global.u32 [%0], %1;" ::"l"(p), "r"(v) : "memory");
+}
+__device__ __forceinline__ void st_release(u64* p, u64 v) {
+  asm volatile("st.release.gpu.global.u64 [%0], %1;" ::"l"(p), "l"(v) : "memory");
+}
+
+// Exclusive scan of n (<= kThreads * per) u32 values in shared memory, in place; returns the
+// total.  All threads of the CTA must call it.  `scratch` holds kWarps + 1 u32.
+__device__ inline u32 block_exclusive_scan(u32* a, int n, u32* scratch) {
+  const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+  const int per = (n + kThreads - 1) / kThreads;
+  const int b = tid * per;
+  u32 sum = 0;
+  for (int i = 0; i < per; i++)
+    if (b + i < n) sum += a[b + i];
+  u32 x = sum;
+#pragma unroll
+  for (int o = 1; o < 32; o <<= 1) {
+    u32 y = __shfl_up_sync(kFull, x, o);
+    if (lane >= o) x += y;
+  }
+  if (lane == 31) scratch[warp] = x;
+  __syncthreads();
+  if (warp == 0) {
+    u32 w = lane < kWarps ? scratch[lane] : 0;
+    u32 s = w;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+      u32 y = __shfl_up_sync(kFull, s, o);
+      if (lane >= o) s += y;
+    }
+    if (lane < kWarps) scratch[lane] = s - w;
+    if (lane == kWarps - 1) scratch[kWarps] = s;
+  }
+  __syncthreads();
+  u32 run = scratch[warp] + x - sum;
+  for (int i = 0; i < per; i++)
+    if (b + i < n) {
+      u32 v = a[b + i];
+      a[b + i] = run;
+      run += v;
+    }
+  u32 total = scratch[kWarps];
+  __syncthreads();
+  return total;
+}
+
+// Same for u64 values.
+__device__ inline u64 block_exclusive_scan64(u64* a, int n, u64* scratch) {
+  const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+  const int per = (n + kThreads - 1) / kThreads;
+  const int b = tid * per;
+  u64 sum = 0;
+  for (int i = 0; i < per; i++)
+    if (b + i < n) sum += a[b + i];
+  u64 x = sum;
+#pragma unroll
+  for (int o = 1; o < 32; o <<= 1) {
+    u64 y = __shfl_up_sync(kFull, x, o);
+    if (lane >= o) x += y;
+  }
+  if (lane == 31) scratch[warp] = x;
+  __syncthreads();
+  if (warp == 0) {
+    u64 w = lane < kWarps ? scratch[lane] : 0;
+    u64 s = w;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+      u64 y = __shfl_up_sync(kFull, s, o);
+      if (lane >= o) s += y;
+    }
+    if (lane < kWarps) scratch[lane] = s - w;
+    if (lane == kWarps - 1) scratch[kWarps] = s;
+  }
+  __syncthreads();
+  u64 run = scratch[warp] + x - sum;
+  for (int i = 0; i < per; i++)
+    if (b + i < n) {
+      u64 v = a[b + i];
+      a[b + i] = run;
+      run += v;
+    }
+  u64 total = scratch[kWarps];
+  __syncthreads();
+  return total;
+}
+
+// Bin of a tile: the last bin whose tile_start <= t (bins are in tile order).
+__device__ __forceinline__ u64 find_bin(const Bin* bins, u64 nb, u64 t) {
+  u64 lo = 0, hi = nb;  // invariant: bins[lo].tile_start <= t < bins[hi].tile_start
+  while (hi - lo > 1) {
+    u64 mid = (lo + hi) >> 1;
+    if (bins[mid].tile_start <= t) lo = mid; else hi = mid;
+  }
+  return lo;
+}
+
+// Copy `words` 8-byte words global -> shared (coalesced, 16-byte loads when aligned).
+__device__ __forceinline__ void load_words(u64* dst, const u64* src, u64 words) {
+  const int tid = threadIdx.x;
+  if ((((uintptr_t)src) & 15) == 0) {
+    const u64 pairs = words >> 1;
+    const ulonglong2* s2 = reinterpret_cast<const ulonglong2*>(src);
+    ulonglong2* d2 = reinterpret_cast<ulonglong2*>(dst);
+    for (u64 i = tid; i < pairs; i += kThreads) d2[i] = __ldcs(s2 + i);
+    if ((words & 1) && tid == 0) dst[words - 1] = __ldcs(src + words - 1);
+  } else {
+    for (u64 i = tid; i < words; i += kThreads) dst[i] = __ldcs(src + i);
+  }
+}
+
+// Copy `words` words shared -> global.
+__device__ __forceinline__ void store_words(u64* dst, const u64* src, u64 words) {
+  const int tid = threadIdx.x;
+  if ((((uintptr_t)dst) & 15) == 0) {
+    const u64 pairs = words >> 1;
+    const ulonglong2* s2 = reinterpret_cast<const ulonglong2*>(src);
+    ulonglong2* d2 = reinterpret_cast<ulonglong2*>(dst);
+    for (u64 i = tid; i < pairs; i += kThreads) d2[i] = s2[i];
+    if ((words & 1) && tid == 0) dst[words - 1] = src[words - 1];
+  } else {
+    for (u64 i = tid; i < words; i += kThreads) dst[i] = src[i];
+  }
+}
+
+// ------------------------------------------------------------------ launch helpers
+// Host-side launchers implemented in the kernel translation units.  Each returns the
+// number of kernels it launched (or -1 on a launch error).
+int launch_init_plain(const Job& j, u32 lo, u32 W, cudaStream_t s);
+int launch_init_single_chunk(const Job& j, cudaStream_t s);
+int launch_init_segments(const Job& j, u32 grid, cudaStream_t s);
+int launch_hist(const Job& j, int level, int mode, u32 grid, cudaStream_t s);
+int launch_scatter(const Job& j, int level, bool wide_status, u32 grid, cudaStream_t s);
+int launch_classify(const Job& j, int level, u32 grid, cudaStream_t s);
+int launch_chunks(const Job& j, u32 grid, cudaStream_t s);
+int launch_copy(const Job& j, u32 grid, cudaStream_t s);
+int launch_read_counts(const Job& j, u64* d_counts, u32 W, cudaStream_t s);
+
+// smem bytes and CTAs per SM of the tile/chunk kernels for a job
+size_t scatter_smem_bytes(const Job& j);
+size_t chunk_smem_bytes(const Job& j);
+int scatter_ctas_per_sm(const Job& j, bool wide_status);
+int chunk_ctas_per_sm(const Job& j);
+int hist_ctas_per_sm(const Job& j);
+
+}  // namespace rsg

@@ -1,0 +1,169 @@
+"""GPU parity: the CUDA sorter against the CPU oracle, byte for byte (-m gpu).
+
+The sorter is stable, so its output is unique and must equal the oracle's stable LSD sort
+exactly.  Sizes span several tiles and chunks with ragged tails; distributions cover the
+degenerate cases of the method (all keys equal, long shared prefixes, heavy duplicates).
+"""
+import numpy as np
+import pytest
+
+import oracle
+import workloads as wl
+
+torch = pytest.importorskip("torch")
+import paper_1703_00687_gb300 as rg  # noqa: E402
+from tests.gpu_checks import from_dev, to_dev  # noqa: E402
+
+pytestmark = pytest.mark.gpu
+
+
+def gsort(a, key_size):
+    t = to_dev(a)
+    rg.sort(t, key_size)
+    torch.cuda.synchronize()
+    rg.check_status()
+    return from_dev(t)
+
+
+def rand(rng, n, R, K, distinct=None):
+    a = rng.integers(0, 256, size=(n, R), dtype=np.uint8)
+    if distinct:
+        pool = rng.integers(0, 256, size=(distinct, K), dtype=np.uint8)
+        a[:, :K] = pool[rng.integers(0, distinct, size=n)]
+    return a
+
+
+# ------------------------------------------------------------------ one pass
+@pytest.mark.parametrize("R,K,lo,w", [(8, 8, 56, 8), (16, 8, 0, 8), (16, 8, 37, 10), (24, 16, 60, 8),
+                                      (24, 16, 120, 8), (32, 8, 3, 5), (40, 13, 90, 9), (64, 16, 64, 1)])
+def test_partition_parity(R, K, lo, w):
+    rng = np.random.default_rng(R * 7 + lo)
+    for n in (2, 511, 4096 * 3 + 17, 100_003):
+        a = rand(rng, n, R, K)
+        src, dst = to_dev(a), torch.empty((n, R), dtype=torch.uint8, device="cuda")
+        rg.partition(src, dst, K, lo, w)
+        torch.cuda.synchronize()
+        rg.check_status()
+        np.testing.assert_array_equal(from_dev(dst), oracle.partition(a, K, lo, w))
+
+
+@pytest.mark.parametrize("R,K,lo,w", [(8, 8, 56, 8), (16, 8, 11, 10), (24, 16, 64, 7)])
+def test_histogram_parity(R, K, lo, w):
+    rng = np.random.default_rng(3)
+    for n in (0, 1, 1000, 300_001):
+        a = rand(rng, n, R, K, distinct=50 if n > 1000 else None)
+        h = rg.histogram(to_dev(a), K, lo, w)
+        torch.cuda.synchronize()
+        np.testing.assert_array_equal(from_dev(h).astype(np.uint64), oracle.histogram(a, K, lo, w))
+
+
+# ---------------------------------------------------------------------- sort
+LAYOUTS = [(8, 8), (8, 1), (8, 5), (16, 8), (16, 16), (24, 16), (32, 8), (40, 13), (64, 16), (256, 9)]
+
+
+@pytest.mark.parametrize("R,K", LAYOUTS)
+def test_sort_parity_sizes(R, K):
+    rng = np.random.default_rng(R * 31 + K)
+    for n in (0, 1, 2, 3, 100, 4095, 4672, 4673, 9000, 70_001, 300_007):
+        a = rand(rng, n, R, K)
+        np.testing.assert_array_equal(gsort(a, K), oracle.sort(a, K), err_msg=f"n={n}")
+
+
+def test_sort_parity_uniform_1e6_r8():
+    a = wl.uniform(1_000_000, 8, 8, seed=1)
+    np.testing.assert_array_equal(gsort(a, 8), oracle.sort(a, 8))
+
+
+@pytest.mark.parametrize("kind", ["all_equal", "two_keys", "sorted", "reverse", "last_byte", "small_ints",
+                                  "few_distinct", "top_bit_only", "long_runs"])
+def test_sort_parity_degenerate(kind):
+    rng = np.random.default_rng(11)
+    n, R, K = 400_000, 16, 8
+    a = rand(rng, n, R, K)
+    keys = a[:, :8].copy().view("<u8").ravel()
+    if kind == "all_equal":
+        keys[:] = 0x0123456789abcdef
+    elif kind == "two_keys":
+        keys[:] = np.where(rng.random(n) < 0.5, 5, 1 << 63)
+    elif kind == "sorted":
+        keys.sort()
+    elif kind == "reverse":
+        keys[:] = np.sort(keys)[::-1]
+    elif kind == "last_byte":
+        keys[:] = 0xabcdef0000000000 | rng.integers(0, 256, n).astype(np.uint64)
+    elif kind == "small_ints":
+        keys[:] = rng.integers(0, 1 << 20, n).astype(np.uint64)
+    elif kind == "few_distinct":
+        keys[:] = rng.integers(0, 1 << 64, 37, dtype=np.uint64)[rng.integers(0, 37, n)]
+    elif kind == "top_bit_only":
+        keys[:] = (rng.integers(0, 2, n).astype(np.uint64) << np.uint64(63))
+    elif kind == "long_runs":
+        keys[:] = np.repeat(rng.integers(0, 1 << 64, n // 5000 + 1, dtype=np.uint64), 5000)[:n]
+    a[:, :8] = keys.view(np.uint8).reshape(n, 8)
+    np.testing.assert_array_equal(gsort(a, K), oracle.sort(a, K))
+
+
+def test_sort_parity_zipf():
+    a = wl.zipf(1_500_000, 16, seed=3)
+    np.testing.assert_array_equal(gsort(a, 8), oracle.sort(a, 8))
+
+
+def test_sort_parity_kmer():
+    a = wl.kmer(1_000_000, 24, seed=4)
+    np.testing.assert_array_equal(gsort(a, 16), oracle.sort(a, 16))
+
+
+def test_sort_parity_kmer_few_prefixes():
+    a = wl.kmer(600_000, 24, seed=9, prefixes=3)
+    np.testing.assert_array_equal(gsort(a, 16), oracle.sort(a, 16))
+
+
+# ----------------------------------------------------------------- segmented
+def test_segmented_parity():
+    rng = np.random.default_rng(5)
+    sizes = np.concatenate([[0, 1, 2, 0], rng.integers(0, 60, 200), rng.integers(1000, 6000, 20),
+                            rng.integers(10_000, 200_000, 4), [0, 1]]).astype(np.uint64)
+    rng.shuffle(sizes)
+    off = np.concatenate([[0], np.cumsum(sizes)]).astype(np.uint64)
+    n = int(off[-1])
+    a = rand(rng, n, 16, 8, distinct=n // 3)
+    t = to_dev(a)
+    offs = torch.from_numpy(off.astype(np.int64)).cuda()
+    rg.sort_segmented(t, offs, 8, total=n)
+    torch.cuda.synchronize()
+    rg.check_status()
+    np.testing.assert_array_equal(from_dev(t), oracle.sort_segmented(a, off, 8))
+
+
+def test_segmented_matches_plain_alone():
+    rng = np.random.default_rng(6)
+    sizes = wl.batched_sizes(n_segs=300, lo=1, hi=50_000, cap=10**9, seed=5)
+    off = np.concatenate([[0], np.cumsum(sizes)]).astype(np.uint64)
+    n = int(off[-1])
+    a = wl.uniform(n, 16, 8, seed=6)
+    t = to_dev(a)
+    rg.sort_segmented(t, torch.from_numpy(off.astype(np.int64)).cuda(), 8, total=n)
+    got = from_dev(t)
+    for s in rng.choice(len(sizes), 25, replace=False):
+        lo, hi = int(off[s]), int(off[s + 1])
+        np.testing.assert_array_equal(got[lo:hi], gsort(a[lo:hi], 8))
+
+
+def test_tmp_and_stream_arguments():
+    rng = np.random.default_rng(8)
+    a = rand(rng, 123_457, 32, 16)
+    t = to_dev(a)
+    tmp = torch.empty_like(t)
+    s = torch.cuda.Stream()
+    with torch.cuda.stream(s):
+        rg.sort(t, 16, tmp=tmp, stream=s)
+    s.synchronize()
+    assert rg.status(s) == 0
+    np.testing.assert_array_equal(from_dev(t), oracle.sort(a, 16))
+
+
+def test_host_tensor_roundtrip():
+    a = wl.uniform(200_000, 16, 8, seed=12)
+    t = torch.from_numpy(a.copy())
+    rg.sort(t, 8)
+    np.testing.assert_array_equal(t.numpy(), oracle.sort(a, 8))

@@ -7,10 +7,10 @@
 //
 // The index sort follows the paper's small/tiny-bin scheme on chip: skip the key bits that
 // every record of the range shares (AND/OR of the keys), then a counting-sort distribution on
-// the next 16 differing bits (two stable 8-bit passes), then the runs of records equal in
-// those bits: runs of up to kEsMax records are finished by enumeration sort (each record's
-// rank = the number of records that must precede it, section 2.2 and 3.3); longer runs whose
-// keys still differ go through the same steps again.  Ties are broken by the record's input
+// the next 16 bits (two stable 8-bit passes), then the runs of records equal in those bits:
+// runs of up to kEsMax records are finished by enumeration sort (each record's rank = the
+// number of records that must precede it, section 2.2 and 3.3); longer runs go through the
+// same steps again (a run whose keys are all equal is already in order).  Ties are broken by the record's input
 // position, so the chunk sort is stable and the whole sorter is stable.
 #include "rs_internal.cuh"
 
@@ -23,7 +23,7 @@ constexpr size_t kChunkSmem = 112 * 1024;
 constexpr size_t kChunkFixed = 2 * 1024 + kWarps * 256 * 2 + 1024;
 
 struct ChunkLayout {
-  size_t stage, permA, permB, hpos, segflag, whist, stack, total;
+  size_t stage, permA, permB, win, whist, stack, total;
 };
 
 __host__ __device__ inline ChunkLayout chunk_layout(u32 m, u32 RW) {
@@ -32,9 +32,7 @@ __host__ __device__ inline ChunkLayout chunk_layout(u32 m, u32 RW) {
   c.stage = o; o += (size_t)m * RW * 8;
   c.permA = o; o += (size_t)m * 2;
   c.permB = o; o += (size_t)m * 2;
-  c.hpos = o; o += (size_t)(m + 1) * 2 + 2;
-  o = (o + 3) & ~(size_t)3;
-  c.segflag = o; o += (size_t)(m / 32 + 1) * 4;
+  c.win = o; o += (size_t)(m + 1) * 2 + 2;
   o = (o + 15) & ~(size_t)15;
   c.whist = o; o += (size_t)kWarps * 256 * 2;
   c.stack = o; o += (size_t)(m / (kEsMax + 1) + 2) * 8;
@@ -44,18 +42,23 @@ __host__ __device__ inline ChunkLayout chunk_layout(u32 m, u32 RW) {
 
 template <int KW, int RWT>
 struct ChunkCtx {
-  const Job* j;
+  u64 km0, km1;   // key bits of words 0 and 1
   u32 RW;
   const u64* stage;
   u16* permA;
   u16* permB;
-  u16* hpos;      // start of each run (relative to the range), then the range size
-  u32* segflag;   // one bit per run: its keys still differ
+  u16* win;       // window digit of each position of the range being sorted
   u16* whist;
   u32* stack;  // pairs (begin, size)
   u32 stack_cap;
 
-  __device__ __forceinline__ Key<KW> key(u32 r) const { return load_key<KW>(stage + (u64)r * RW, *j); }
+  __device__ __forceinline__ Key<KW> key(u32 r) const {
+    const u64* p = stage + r * (RWT ? (u32)RWT : RW);
+    Key<KW> k;
+    k.w[0] = p[0] & km0;
+    if (KW == 2) k.w[KW - 1] = p[1] & km1;
+    return k;
+  }
 };
 
 // Stable counting sort of positions [a, a + s) of `src` into `dst` by key bits [lo, lo + w).
@@ -113,12 +116,9 @@ __device__ void lsd_pass(const ChunkCtx<KW, RWT>& c, const u16* src, u16* dst, u
 }
 
 // Sort positions [a, a + s) of permA by the full key, given that every key bit >= p is
-// shared by the range.  Runs longer than kEsMax whose keys still differ are pushed on the
-// stack for another round.
+// shared by the range.  Runs longer than kEsMax go on the stack for another round.
 template <int KW, int RWT>
 __device__ void sort_round(const ChunkCtx<KW, RWT>& c, u32 a, u32 s, u32 p, u32* s_top) {
-  __shared__ u32 scr[kWarps + 1];
-  __shared__ u32 s_nseg;
   const int tid = threadIdx.x;
   const u32 lo1 = p > 16 ? p - 16 : 0;
   const u32 wall = p - lo1;
@@ -132,87 +132,74 @@ __device__ void sort_round(const ChunkCtx<KW, RWT>& c, u32 a, u32 s, u32 p, u32*
     for (u32 i = tid; i < s; i += kThreads) c.permA[a + i] = c.permB[a + i];
     __syncthreads();
   }
-  // runs of equal key bits [lo1, p): run starts by a scan of head flags over contiguous
-  // per-thread slices
-  const u32 per = (s + kThreads - 1) / kThreads;
-  const u32 b0 = min(s, tid * per), b1 = min(s, b0 + per);
-  u32 heads = 0;
-  for (u32 i = b0; i < b1; i++)
-    heads += i == 0 || digit_of<KW>(c.key(c.permA[a + i]), lo1, wall) != digit_of<KW>(c.key(c.permA[a + i - 1]), lo1, wall);
-  {
-    const int lane = tid & 31, warp = tid >> 5;
-    u32 x = heads;
-#pragma unroll
-    for (int o = 1; o < 32; o <<= 1) {
-      const u32 y = __shfl_up_sync(kFull, x, o);
-      if (lane >= o) x += y;
-    }
-    if (lane == 31) scr[warp] = x;
-    __syncthreads();
-    if (warp == 0) {
-      const u32 wv = lane < kWarps ? scr[lane] : 0;
-      u32 t = wv;
-#pragma unroll
-      for (int o = 1; o < 32; o <<= 1) {
-        const u32 y = __shfl_up_sync(kFull, t, o);
-        if (lane >= o) t += y;
-      }
-      if (lane < kWarps) scr[lane] = t - wv;
-      if (lane == kWarps - 1) s_nseg = t;
-    }
-    __syncthreads();
-    u32 seg = scr[warp] + x - heads;  // runs begun before this slice
-    for (u32 i = b0; i < b1; i++) {
-      if (i == 0 || digit_of<KW>(c.key(c.permA[a + i]), lo1, wall) != digit_of<KW>(c.key(c.permA[a + i - 1]), lo1, wall))
-        c.hpos[seg++] = (u16)i;
-    }
-  }
+  // window digit (key bits [lo1, p)) of every position: non-decreasing along the range, so a
+  // run of equal digits is found by looking at neighbours and by binary search
+  u16* win = c.win;
+  for (u32 i = tid; i < s; i += kThreads) win[i] = (u16)digit_of<KW>(c.key(c.permA[a + i]), lo1, wall);
   __syncthreads();
-  const u32 nseg = s_nseg;
-  if (tid == 0) c.hpos[nseg] = (u16)s;
-  for (u32 i = tid; i < nseg / 32 + 1; i += kThreads) c.segflag[i] = 0;
-  __syncthreads();
-  // run of relative position i: the last run start <= i (binary search over hpos)
-  auto run_of = [&](u32 i) {
-    u32 lo = 0, hi = nseg;  // hpos[lo] <= i < hpos[hi]
-    while (hi - lo > 1) {
-      const u32 mid = (lo + hi) >> 1;
-      if (c.hpos[mid] <= i) lo = mid; else hi = mid;
-    }
-    return lo;
-  };
-  // enumeration sort of short runs into permB; mark long runs whose keys differ
   for (u32 i = tid; i < s; i += kThreads) {
-    const u32 sg = run_of(i);
-    const u32 st = c.hpos[sg], en = c.hpos[sg + 1], sz = en - st;
-    if (sz < 2) continue;
+    const u32 d = win[i];
     const u32 r = c.permA[a + i];
-    const Key<KW> kr = c.key(r);
-    if (sz <= (u32)kEsMax) {
-      u32 rank = 0;
-      for (u32 q = st; q < en; q++) {
-        const u32 r2 = c.permA[a + q];
-        const Key<KW> k2 = c.key(r2);
-        rank += key_less<KW>(k2, kr) || (key_eq<KW>(k2, kr) && r2 < r);
-      }
-      c.permB[a + st + rank] = (u16)r;
-    } else if (!key_eq<KW>(kr, c.key(c.permA[a + st]))) {
-      atomicOr(&c.segflag[sg >> 5], 1u << (sg & 31));
+    const bool head = i == 0 || win[i - 1] != d;
+    const bool last = i + 1 == s || win[i + 1] != d;
+    if (head && last) {  // a run of one record
+      c.permB[a + i] = (u16)r;
+      continue;
     }
+    // run start: first position with digit d in [i - kEsMax, i]
+    bool lng = false;
+    u32 st = i, en = i + 1;
+    const u32 L = i >= (u32)kEsMax ? i - kEsMax : 0;
+    if (i >= (u32)kEsMax && win[L] == d) {
+      lng = true;
+    } else {
+      u32 lo = L, hi = i;
+      while (lo < hi) {
+        const u32 mid = (lo + hi) >> 1;
+        if (win[mid] < d) lo = mid + 1; else hi = mid;
+      }
+      st = lo;
+      const u32 H = min(s - 1, i + kEsMax);
+      if (i + kEsMax < s && win[H] == d) {
+        lng = true;
+      } else {
+        u32 lo2 = i + 1, hi2 = H + 1;
+        while (lo2 < hi2) {
+          const u32 mid = (lo2 + hi2) >> 1;
+          if (win[mid] <= d) lo2 = mid + 1; else hi2 = mid;
+        }
+        en = lo2;
+        lng = en - st > (u32)kEsMax;
+      }
+    }
+    if (lng) {  // stays in place for now; its head measures it and pushes it
+      c.permB[a + i] = (u16)r;
+      if (head) {
+        u32 lo2 = i + 1, hi2 = s;
+        while (lo2 < hi2) {
+          const u32 mid = (lo2 + hi2) >> 1;
+          if (win[mid] <= d) lo2 = mid + 1; else hi2 = mid;
+        }
+        const u32 t = atomicAdd(s_top, 1u);
+        if (t < c.stack_cap) {
+          c.stack[2 * t] = a + i;
+          c.stack[2 * t + 1] = lo2 - i;
+        }
+      }
+      continue;
+    }
+    // enumeration sort: rank = records of the run that must precede this one
+    const Key<KW> kr = c.key(r);
+    u32 rank = 0;
+    for (u32 q = st; q < en; q++) {
+      const u32 r2 = c.permA[a + q];
+      const Key<KW> k2 = c.key(r2);
+      rank += key_less<KW>(k2, kr) || (key_eq<KW>(k2, kr) && r2 < r);
+    }
+    c.permB[a + st + rank] = (u16)r;
   }
   __syncthreads();
-  for (u32 i = tid; i < s; i += kThreads) {
-    const u32 sg = run_of(i);
-    const u32 st = c.hpos[sg], en = c.hpos[sg + 1], sz = en - st;
-    if (sz >= 2 && sz <= (u32)kEsMax) c.permA[a + i] = c.permB[a + i];
-    if (sz > (u32)kEsMax && i == st && ((c.segflag[sg >> 5] >> (sg & 31)) & 1u)) {
-      const u32 t = atomicAdd(s_top, 1u);
-      if (t < c.stack_cap) {
-        c.stack[2 * t] = a + st;
-        c.stack[2 * t + 1] = sz;
-      }
-    }
-  }
+  for (u32 i = tid; i < s; i += kThreads) c.permA[a + i] = c.permB[a + i];
   __syncthreads();
 }
 
@@ -269,14 +256,14 @@ __global__ void __launch_bounds__(kThreads, 2) k_chunk(Job j) {
   const ChunkLayout lay = chunk_layout(m, RW);
   extern __shared__ __align__(16) unsigned char smem[];
   ChunkCtx<KW, RWT> c;
-  c.j = &j;
+  c.km0 = j.keymask[0];
+  c.km1 = j.keymask[1];
   c.RW = RW;
   u64* stage = (u64*)(smem + lay.stage);
   c.stage = stage;
   c.permA = (u16*)(smem + lay.permA);
   c.permB = (u16*)(smem + lay.permB);
-  c.hpos = (u16*)(smem + lay.hpos);
-  c.segflag = (u32*)(smem + lay.segflag);
+  c.win = (u16*)(smem + lay.win);
   c.whist = (u16*)(smem + lay.whist);
   c.stack = (u32*)(smem + lay.stack);
   c.stack_cap = m / (kEsMax + 1) + 2;
@@ -297,7 +284,8 @@ __global__ void __launch_bounds__(kThreads, 2) k_chunk(Job j) {
     }
     const u64* src = j.buf[(ch.flags & kChSrcTmp) ? 1 : 0] + ch.begin * RW;
     u64* dst = j.buf[0] + ch.begin * RW;
-    load_words(stage, src, (u64)sz * RW);
+    load_words_async(stage, src, (u64)sz * RW);
+    cp_async_wait_all();
     __syncthreads();
     u32 p = 0;
     if (!(ch.flags & kChCopyOnly)) p = range_top_bit(c, 0, sz, false);
@@ -428,7 +416,7 @@ int launch_copy(const Job& j, u32 grid, cudaStream_t s) {
 // shared memory of two CTAs per SM.
 u32 chunk_capacity(u32 RW) {
   const size_t budget = kChunkSmem - kChunkFixed;
-  u32 m = (u32)((budget * 8) / (RW * 64 + 49));   // R + 6 bytes + 1 bit per record
+  u32 m = (u32)(budget / (RW * 8 + 6));   // the record + three u16 index arrays
   m &= ~63u;
   if (m > (u32)kThreads * kChunkItems) m = kThreads * kChunkItems;
   return m;

@@ -44,8 +44,8 @@ struct Bin {
   u64 tile_start;   // number of the bin's first tile within its level
   u64 base_off;     // first of its 2^W entries in the level's bucket-base pool
   u64 status_off;   // first of its tiles * 2^W look-back words
-  u64 kand[2];      // AND / OR of the bin's keys (level 0 only: picks the first useful digit)
-  u64 kor[2];
+  u64 kand[2];      // AND / OR of the bin's keys, gathered by the histogram pass: they tell
+  u64 kor[2];       // whether the digit starts at the highest differing bit, or all keys are equal
   u32 lo, W;        // the digit is key bits [lo, lo + W)
   u32 parity;       // 0: the bin's records are in `in`; 1: in `tmp`
   u32 flags;
@@ -80,8 +80,7 @@ struct Ctl {
   u64 status_used[2];
   u64 s_ticket;     // tile dispenser of the scatter pass
   u32 cls_done;     // classify CTAs finished (the last one finalises the next list)
-  u32 pad1;
-  u64 mslot_used;   // mask slots handed out this level
+  u32 nredo;        // bins of this level whose digit moved after the count (recount needed)
   u64 nchunks, chunk_ticket;
   u64 npieces, piece_ticket;
   u32 never;        // stays 0: the word an injected stall waits on
@@ -106,10 +105,8 @@ struct Job {
   Ctl* ctl;
   Bin* bins[2];
   u64 cap_bins;
-  u64* base[2];       // bucket counts, then (after the scan) bases | (mask slot + 1) << 40
+  u64* base[2];       // bucket counts, then (after the scan) bucket bases
   u64 cap_base;
-  u64* masks;         // per mask slot: AND[KW], OR[KW]
-  u64 cap_mslots;
   void* status[2];    // look-back words (u32 or u64)
   u64 cap_status;
   Chunk* chunks;
@@ -120,8 +117,6 @@ struct Job {
   u64 n_segs;
 };
 
-constexpr u64 kBaseMask = (1ull << 40) - 1;   // bucket base (records)
-constexpr int kSlotShift = 40;                 // mask slot + 1 above it (0 = none)
 constexpr u64 kPieceRecords = 1ull << 16;      // copy-back granularity
 
 // ---------------------------------------------------------------------------- keys
@@ -224,11 +219,13 @@ __device__ __forceinline__ void st_release(u64* p, u64 v) {
   asm volatile("st.release.gpu.global.u64 [%0], %1;" ::"l"(p), "l"(v) : "memory");
 }
 
-// Exclusive scan of n (<= kThreads * per) u32 values in shared memory, in place; returns the
-// total.  All threads of the CTA must call it.  `scratch` holds kWarps + 1 u32.
+// Exclusive scan of n u32 values in shared memory, in place, by a CTA of NT threads; returns
+// the total.  All threads of the CTA must call it.  `scratch` holds NT/32 + 1 u32.
+template <int NT = kThreads>
 __device__ inline u32 block_exclusive_scan(u32* a, int n, u32* scratch) {
+  constexpr int kW = NT / 32;
   const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
-  const int per = (n + kThreads - 1) / kThreads;
+  const int per = (n + NT - 1) / NT;
   const int b = tid * per;
   u32 sum = 0;
   for (int i = 0; i < per; i++)
@@ -242,15 +239,15 @@ __device__ inline u32 block_exclusive_scan(u32* a, int n, u32* scratch) {
   if (lane == 31) scratch[warp] = x;
   __syncthreads();
   if (warp == 0) {
-    u32 w = lane < kWarps ? scratch[lane] : 0;
+    u32 w = lane < kW ? scratch[lane] : 0;
     u32 s = w;
 #pragma unroll
     for (int o = 1; o < 32; o <<= 1) {
       u32 y = __shfl_up_sync(kFull, s, o);
       if (lane >= o) s += y;
     }
-    if (lane < kWarps) scratch[lane] = s - w;
-    if (lane == kWarps - 1) scratch[kWarps] = s;
+    if (lane < kW) scratch[lane] = s - w;
+    if (lane == kW - 1) scratch[kW] = s;
   }
   __syncthreads();
   u32 run = scratch[warp] + x - sum;
@@ -260,7 +257,7 @@ __device__ inline u32 block_exclusive_scan(u32* a, int n, u32* scratch) {
       a[b + i] = run;
       run += v;
     }
-  u32 total = scratch[kWarps];
+  u32 total = scratch[kW];
   __syncthreads();
   return total;
 }
@@ -313,6 +310,32 @@ __device__ __forceinline__ u64 find_bin(const Bin* bins, u64 nb, u64 t) {
     if (bins[mid].tile_start <= t) lo = mid; else hi = mid;
   }
   return lo;
+}
+
+// Asynchronous global -> shared copies (cp.async, completed by cp_async_wait_all): all of a
+// tile's loads are in flight at once, without staging through registers.
+__device__ __forceinline__ void cp_async16(void* smem, const void* gmem) {
+  const unsigned s = (unsigned)__cvta_generic_to_shared(smem);
+  asm volatile("cp.async.cg.shared.global [%0], [%1], 16;\n" ::"r"(s), "l"(gmem) : "memory");
+}
+__device__ __forceinline__ void cp_async8(void* smem, const void* gmem) {
+  const unsigned s = (unsigned)__cvta_generic_to_shared(smem);
+  asm volatile("cp.async.ca.shared.global [%0], [%1], 8;\n" ::"r"(s), "l"(gmem) : "memory");
+}
+__device__ __forceinline__ void cp_async_wait_all() { asm volatile("cp.async.wait_all;\n" ::: "memory"); }
+
+// Start copying `words` 8-byte words global -> shared (16-byte copies when the source is
+// 16-byte aligned; the destination always is).  Call cp_async_wait_all + __syncthreads
+// before reading them.
+__device__ __forceinline__ void load_words_async(u64* dst, const u64* src, u64 words) {
+  const int tid = threadIdx.x;
+  if ((((uintptr_t)src) & 15) == 0) {
+    const u64 pairs = words >> 1;
+    for (u64 i = tid; i < pairs; i += kThreads) cp_async16(dst + 2 * i, src + 2 * i);
+    if ((words & 1) && tid == 0) cp_async8(dst + words - 1, src + words - 1);
+  } else {
+    for (u64 i = tid; i < words; i += kThreads) cp_async8(dst + i, src + i);
+  }
 }
 
 // Copy `words` 8-byte words global -> shared (coalesced, 16-byte loads when aligned).

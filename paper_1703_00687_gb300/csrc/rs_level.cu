@@ -156,6 +156,8 @@ __global__ void __launch_bounds__(kThreads) k_init_segments(Job j) {
 __global__ void __launch_bounds__(kThreads) k_finalize0(Job j) { finalize_list(j, 0); }
 
 // ------------------------------------------------------------------- histogram
+constexpr int kHistItems = 8;  // records per thread per tile (T <= kThreads * kHistItems)
+
 // The last CTA to count a bin: at level 0 check that the digit starts at the bin's highest
 // differing key bit (else move it there and ask for a recount); then counts -> bases, and a
 // mask slot for every sub-bin that will need another pass.
@@ -328,18 +330,26 @@ __global__ void __launch_bounds__(kThreads) k_hist(Job j, int level, int mode) {
       }
     }
     const u64* src = j.buf[bp->parity] + bp->begin * j.RW;
-    for (u64 base = r0; base < r1; base += kThreads) {
-      const u64 r = base + tid;
+    // all of the tile's key loads in flight before any is used
+    Key<KW> keys[kHistItems];
+#pragma unroll
+    for (int it = 0; it < kHistItems; it++) {
+      const u64 r = r0 + (u64)it * kThreads + tid;
+      if (r < r1) keys[it] = load_key<KW>(src + r * j.RW, j);
+    }
+#pragma unroll
+    for (int it = 0; it < kHistItems; it++) {
+      const u64 r = r0 + (u64)it * kThreads + tid;
+      if (r0 + (u64)it * kThreads >= r1) break;  // uniform
       const bool valid = r < r1;
       u32 d = 0;
       if (valid) {
-        const Key<KW> k = load_key<KW>(src + r * j.RW, j);
-        d = digit_of<KW>(k, lo, W);
+        d = digit_of<KW>(keys[it], lo, W);
         if (want_masks) {
 #pragma unroll
           for (int q = 0; q < KW; q++) {
-            kand[q] &= k.w[q];
-            kor[q] |= k.w[q];
+            kand[q] &= keys[it].w[q];
+            kor[q] |= keys[it].w[q];
           }
         }
       }
@@ -363,7 +373,7 @@ __host__ __device__ inline ScatterLayout scatter_layout(u32 T, u32 RW, u32 KW, u
   size_t o = 0;
   s.stage = o; o += (size_t)T * RW * 8;
   s.gbase = o; o += nd * 8;
-  s.sand = o; o += nd * KW * 8;
+  s.sand = o; o += nd * KW * 8;   // AND of the keys per digit, as 2*KW 32-bit halves
   s.sor = o; o += nd * KW * 8;
   s.tcount = o; o += nd * 4;
   s.tbase = o; o += nd * 4;
@@ -437,28 +447,55 @@ __global__ void __launch_bounds__(kThreads) k_scatter(Job j, int level) {
   extern __shared__ __align__(16) unsigned char smem[];
   u64* stage = (u64*)(smem + lay.stage);
   u64* gbase = (u64*)(smem + lay.gbase);
-  u64* sand = (u64*)(smem + lay.sand);
-  u64* sor = (u64*)(smem + lay.sor);
+  u32* sand = (u32*)(smem + lay.sand);  // [v][2*KW] 32-bit halves: native shared atomics
+  u32* sor = (u32*)(smem + lay.sor);
   u32* tcount = (u32*)(smem + lay.tcount);
   u32* tbase = (u32*)(smem + lay.tbase);
   u32* need = (u32*)(smem + lay.need);
   u16* whist = (u16*)(smem + lay.whist);
   u16* perm = (u16*)(smem + lay.perm);
   u16* sdig = (u16*)(smem + lay.sdig);
-  __shared__ u64 s_ticket;
+  __shared__ u64 s_ticket, s_bin;
   __shared__ u32 scan_scr[kWarps + 1];
   const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
   const u32 its = T / kThreads;
   const u32 per_warp = T / kWarps;
+  // Sub-bin key AND/OR accumulate in shared memory over all tiles this CTA takes from one
+  // bin, and go to global memory once per (CTA, bin).
+  u64 mask_bin = ~0ull;
+  auto flush_masks = [&](u64 mb) {
+    const Bin* mp = &bins[mb];
+    const u32 mnd = 1u << mp->W;
+    const u64* mbase = j.base[L] + mp->base_off;
+    for (u32 v = tid; v < mnd; v += kThreads) {
+      if (!((need[v >> 5] >> (v & 31)) & 1u)) continue;
+      const u64 slot = mbase[v] >> kSlotShift;
+      u64* m = j.masks + (slot - 1) * 2 * KW;
+#pragma unroll
+      for (int q = 0; q < KW; q++) {
+        const u64 a = ((u64)sand[v * 2 * KW + 2 * q + 1] << 32) | sand[v * 2 * KW + 2 * q];
+        const u64 o = ((u64)sor[v * 2 * KW + 2 * q + 1] << 32) | sor[v * 2 * KW + 2 * q];
+        if (o | ~a) {  // skip untouched entries
+          atomicAnd(&m[q], a);
+          atomicOr(&m[KW + q], o);
+        }
+      }
+    }
+  };
 
   for (;;) {
-    if (tid == 0) s_ticket = atomicAdd(&ctl->s_ticket, 1ull);
+    if (tid == 0) {
+      const u64 tk = atomicAdd(&ctl->s_ticket, 1ull);
+      s_ticket = tk;
+      s_bin = tk < ntiles ? find_bin(bins, nb, tk) : 0;
+    }
     __syncthreads();
     const u64 t = s_ticket;
+    const u64 b = s_bin;
     __syncthreads();  // every thread has its ticket before thread 0 may take the next
     if (t >= ntiles) break;
-    const u64 b = find_bin(bins, nb, t);
-    const Bin* bp = &bins[b];
+    const Bin bin = bins[b];
+    const Bin* bp = &bin;
     if (bp->flags & kBinEqual) continue;
     const u32 lo = bp->lo, W = bp->W, nd = 1u << W;
     const u64 tib = t - bp->tile_start;
@@ -468,20 +505,26 @@ __global__ void __launch_bounds__(kThreads) k_scatter(Job j, int level) {
     u64* dstb = j.buf[bp->parity ^ 1];
     const u64* bbase = j.base[L] + bp->base_off;
 
-    load_words(stage, src, (u64)cnt * RW);
+    load_words_async(stage, src, (u64)cnt * RW);
     for (u32 i = tid; i < (u32)kWarps * nd; i += kThreads) whist[i] = 0;
-    for (u32 i = tid; i < nd / 32 + 1; i += kThreads) need[i] = 0;
-    __syncthreads();
-    for (u32 v = tid; v < nd; v += kThreads) {
-      if (bbase[v] >> kSlotShift) {
-        atomicOr(&need[v >> 5], 1u << (v & 31));
+    if (b != mask_bin) {
+      if (mask_bin != ~0ull) flush_masks(mask_bin);
+      __syncthreads();
+      for (u32 i = tid; i < nd / 32 + 1; i += kThreads) need[i] = 0;
+      __syncthreads();
+      for (u32 v = tid; v < nd; v += kThreads) {
+        if (bbase[v] >> kSlotShift) {
+          atomicOr(&need[v >> 5], 1u << (v & 31));
 #pragma unroll
-        for (int k = 0; k < KW; k++) {
-          sand[v * KW + k] = ~0ull;
-          sor[v * KW + k] = 0;
+          for (int k = 0; k < 2 * KW; k++) {
+            sand[v * 2 * KW + k] = ~0u;
+            sor[v * 2 * KW + k] = 0;
+          }
         }
       }
+      mask_bin = b;
     }
+    cp_async_wait_all();
     __syncthreads();
 
     // stable rank: warp w owns records [w*per_warp, (w+1)*per_warp), visited in order
@@ -516,8 +559,10 @@ __global__ void __launch_bounds__(kThreads) k_scatter(Job j, int level) {
               const u32 olo = __reduce_or_sync(peers, (u32)k.w[q]);
               const u32 ohi = __reduce_or_sync(peers, (u32)(k.w[q] >> 32));
               if (before == 0) {
-                atomicAnd(&sand[d * KW + q], ((u64)ahi << 32) | alo);
-                atomicOr(&sor[d * KW + q], ((u64)ohi << 32) | olo);
+                atomicAnd(&sand[d * 2 * KW + 2 * q], alo);
+                atomicAnd(&sand[d * 2 * KW + 2 * q + 1], ahi);
+                atomicOr(&sor[d * 2 * KW + 2 * q], olo);
+                atomicOr(&sor[d * 2 * KW + 2 * q + 1], ohi);
               }
             }
           }
@@ -547,17 +592,7 @@ __global__ void __launch_bounds__(kThreads) k_scatter(Job j, int level) {
         excl = look_back<u64>((u64*)j.status[L], self, nd, tib, tcount[v], j, stall);
       else
         excl = look_back<u32>((u32*)j.status[L], self, nd, tib, tcount[v], j, stall);
-      const u64 e = bbase[v];
-      gbase[v] = bp->begin + (e & kBaseMask) + excl - tbase[v];
-      const u64 slot = e >> kSlotShift;
-      if (slot && tcount[v]) {
-        u64* m = j.masks + (slot - 1) * 2 * KW;
-#pragma unroll
-        for (int q = 0; q < KW; q++) {
-          atomicAnd(&m[q], sand[v * KW + q]);
-          atomicOr(&m[KW + q], sor[v * KW + q]);
-        }
-      }
+      gbase[v] = bp->begin + (bbase[v] & kBaseMask) + excl - tbase[v];
     }
 #pragma unroll
     for (int it = 0; it < kMaxItems; it++) {
@@ -603,6 +638,7 @@ __global__ void __launch_bounds__(kThreads) k_scatter(Job j, int level) {
     if (bad) atomicOr(&ctl->err, kErrInternal);
     __syncthreads();
   }
+  if (mask_bin != ~0ull) flush_masks(mask_bin);
 }
 
 // -------------------------------------------------------------------- classify
@@ -811,7 +847,13 @@ int scatter_ctas_per_sm(const Job& j, bool) {
   return n;
 }
 
-int hist_ctas_per_sm(const Job&) { return 2; }
+int hist_ctas_per_sm(const Job& j) {
+  int n = 0;
+  cudaError_t e = j.KW == 1 ? cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, k_hist<1>, kThreads, 0)
+                            : cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, k_hist<2>, kThreads, 0);
+  if (e != cudaSuccess || n < 1) n = 1;
+  return n;
+}
 
 int launch_init_plain(const Job& j, u32 lo, u32 W, cudaStream_t s) {
   k_init_plain<<<1, kThreads, 0, s>>>(j, lo, W);

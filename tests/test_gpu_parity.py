@@ -84,7 +84,7 @@ def test_sort_parity_degenerate(kind):
     if kind == "all_equal":
         keys[:] = 0x0123456789abcdef
     elif kind == "two_keys":
-        keys[:] = np.where(rng.random(n) < 0.5, 5, 1 << 63)
+        keys[:] = np.where(rng.random(n) < 0.5, np.uint64(5), np.uint64(1 << 63))
     elif kind == "sorted":
         keys.sort()
     elif kind == "reverse":

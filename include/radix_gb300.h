@@ -126,7 +126,7 @@ rs_status radix_sort_release(void);
  */
 typedef struct rs_plan {
   uint32_t digit_bits_max;  /* widest digit of a distribution pass: 8..10 */
-  uint32_t tile_records;    /* records per scatter tile: 512..4096, a multiple of 512 */
+  uint32_t tile_records;    /* records per distribution tile: 512, 1024, 2048 or 4096 */
   uint32_t chunk_records;   /* largest bin sorted on chip: 64.. the shared-memory maximum */
   uint32_t sm_limit;        /* use at most this many SMs for the persistent grids */
   uint32_t watchdog_polls;  /* polls of a look-back wait before it gives up */
@@ -149,7 +149,7 @@ uint64_t radix_sort_launch_count(void);
 enum {
   RS_K_INIT = 0,      /* set-up of the control block, first bin list or chunk */
   RS_K_HIST = 1,      /* histogram of a level's digit (+ bucket bases) */
-  RS_K_HIST_REDO = 2, /* level-0 recount when the first digit had to move */
+  RS_K_HIST_REDO = 2, /* recount of the bins whose digit had to move after the count */
   RS_K_SCATTER = 3,   /* stable distribution of a level's bins (the dominant kernel) */
   RS_K_CLASSIFY = 4,  /* sub-bin classification and the next level's bin list */
   RS_K_CHUNK = 5,     /* on-chip sorts of small bins */

@@ -45,18 +45,17 @@ static int sm_count(int dev) {
 
 // Sizes of every workspace region for a job.
 struct Caps {
-  u64 bins, base, mslots, status, chunks, pieces;
+  u64 bins, base, status, chunks, pieces;
   size_t bytes;
-  size_t off_ctl, off_bins0, off_bins1, off_base0, off_base1, off_masks, off_status, off_chunks, off_pieces;
+  size_t off_ctl, off_bins0, off_bins1, off_base0, off_base1, off_status, off_chunks, off_pieces;
 };
 
 static size_t al(size_t x) { return (x + 255) & ~(size_t)255; }
 
-static Caps caps_for(u64 n, u32 T, u32 cm, u32 wmax, u32 KW, bool wide, u64 n_segs) {
+static Caps caps_for(u64 n, u32 T, u32 cm, u32 wmax, bool wide, u64 n_segs) {
   Caps c;
   c.bins = n / ((u64)cm + 1) + 2;
   c.base = 256ull * c.bins + 2 * (n / cm) + (1ull << wmax) + 64;
-  c.mslots = n / ((u64)cm + 1) + 2;
   c.status = (n / T + c.bins) * (1ull << wmax) + 64;
   c.chunks = 6 * (n / cm) + n_segs + 16;
   c.pieces = n / kPieceRecords + n / ((u64)cm + 1) + 16;
@@ -66,7 +65,6 @@ static Caps caps_for(u64 n, u32 T, u32 cm, u32 wmax, u32 KW, bool wide, u64 n_se
   c.off_bins1 = o; o = al(o + c.bins * sizeof(Bin));
   c.off_base0 = o; o = al(o + c.base * 8);
   c.off_base1 = o; o = al(o + c.base * 8);
-  c.off_masks = o; o = al(o + c.mslots * 2 * KW * 8);
   c.off_status = o; o = al(o + c.status * (wide ? 8 : 4));
   c.off_chunks = o; o = al(o + c.chunks * sizeof(Chunk));
   c.off_pieces = o; o = al(o + c.pieces * sizeof(Piece));
@@ -179,7 +177,7 @@ static rs_status setup_job(void* in, void* tmp, u64 n, u32 rec_size, u32 key_siz
   j.inject = g_inject.exchange(0);
   j.wide = n >= (1ull << 30) ? 1u : 0u;  // 64-bit look-back words for bins of 2^30 records or more
   j.n_segs = n_segs;
-  Caps c = caps_for(n, j.T, j.chunk_max, j.wmax, j.KW, j.wide != 0, n_segs);
+  Caps c = caps_for(n, j.T, j.chunk_max, j.wmax, j.wide != 0, n_segs);
   Workspace* w = nullptr;
   rs_status r = get_workspace(dev, stream, c.bytes, &w);
   if (r != RS_OK) return r;
@@ -191,8 +189,6 @@ static rs_status setup_job(void* in, void* tmp, u64 n, u32 rec_size, u32 key_siz
   j.base[0] = (u64*)(base + c.off_base0);
   j.base[1] = (u64*)(base + c.off_base1);
   j.cap_base = c.base;
-  j.masks = (u64*)(base + c.off_masks);
-  j.cap_mslots = c.mslots;
   j.status[0] = j.status[1] = base + c.off_status;
   j.cap_status = c.status;
   j.chunks = (Chunk*)(base + c.off_chunks);
@@ -265,7 +261,7 @@ static rs_status run_levels(const Setup& st, cudaStream_t s) {
   const int levels = (int)j.K;  // each level consumes >= 8 key bits
   for (int lv = 0; lv < levels; lv++) {
     if (timed(RS_K_HIST, lv, s, [&] { return launch_hist(j, lv, 0, gh, s); }) < 0) return RS_ERR_CUDA;
-    if (lv == 0 && timed(RS_K_HIST_REDO, lv, s, [&] { return launch_hist(j, 0, 1, gh, s); }) < 0) return RS_ERR_CUDA;
+    if (timed(RS_K_HIST_REDO, lv, s, [&] { return launch_hist(j, lv, 1, gh, s); }) < 0) return RS_ERR_CUDA;
     if (timed(RS_K_SCATTER, lv, s, [&] { return launch_scatter(j, lv, j.wide != 0, gs, s); }) < 0) return RS_ERR_CUDA;
     if (timed(RS_K_CLASSIFY, lv, s, [&] { return launch_classify(j, lv, gc, s); }) < 0) return RS_ERR_CUDA;
   }
@@ -438,7 +434,9 @@ rs_status radix_sort_set_plan(const rs_plan* plan) {
   if (!plan) return RS_ERR_INVALID_ARG;
   rs_plan p = *plan;
   if (p.digit_bits_max && (p.digit_bits_max < (u32)kWMin || p.digit_bits_max > (u32)kWMax)) return RS_ERR_INVALID_ARG;
-  if (p.tile_records && (p.tile_records < 512 || p.tile_records > 4096 || p.tile_records % 512)) return RS_ERR_INVALID_ARG;
+  if (p.tile_records && p.tile_records != 512 && p.tile_records != 1024 && p.tile_records != 2048 &&
+      p.tile_records != 4096)
+    return RS_ERR_INVALID_ARG;
   if (p.chunk_records && p.chunk_records < 64) return RS_ERR_INVALID_ARG;
   std::lock_guard<std::mutex> lk(g_mu);
   g_plan = p;

@@ -5,36 +5,41 @@
 // is sorted, and the records are written once, in order, to `in`.  Because every record is
 // staged before any is written, the chunk may be sorted in place.
 //
-// The index sort follows the paper's small/tiny-bin scheme on chip: skip the key bits that
-// every record of the range shares (AND/OR of the keys), then a counting-sort distribution on
-// the next 16 bits (two stable 8-bit passes), then the runs of records equal in those bits:
-// runs of up to kEsMax records are finished by enumeration sort (each record's rank = the
-// number of records that must precede it, section 2.2 and 3.3); longer runs go through the
-// same steps again (a run whose keys are all equal is already in order).  Ties are broken by the record's input
-// position, so the chunk sort is stable and the whole sorter is stable.
+// The index sort follows the paper's small/tiny-bin scheme on chip:
+//   * skip the key bits every record of the range shares (AND/OR of the keys);
+//   * one counting-sort distribution on the next kWinBits bits, with shared-memory atomic
+//     counters (the order inside a bucket is arbitrary here);
+//   * every bucket of up to kEsMax records is finished by enumeration sort (section 2.2,
+//     3.3): a record's place is the number of records of the bucket that must precede it,
+//     comparing (key, input position) -- so equal keys come out in input order;
+//   * a larger bucket is processed again the same way; if all its keys are equal it is put
+//     back in input order by one counting pass on the (unique) input positions.
+// The result is therefore the stable order, and the whole sorter is stable.
 #include "rs_internal.cuh"
 
 namespace rsg {
 
-constexpr int kEsMax = 48;           // longest run finished by enumeration sort
-constexpr int kChunkItems = 12;      // index-sort items per thread (chunk_max <= 512 * 12)
+constexpr int kEsMax = 48;       // largest bucket finished by enumeration sort
+constexpr int kWinBits = 12;     // digit of the on-chip distribution pass
+constexpr int kIdxBits = 13;     // input positions of a chunk (chunk_max <= 2^13)
+constexpr int kChunkItems = 12;  // positions per thread (chunk_max <= 512 * 12)
+constexpr int kCntWords = 1 << (kIdxBits - 1);  // two 16-bit counters per word
 // per-CTA shared memory the chunk kernel may use (two CTAs per SM), and what is not per record
 constexpr size_t kChunkSmem = 112 * 1024;
-constexpr size_t kChunkFixed = 2 * 1024 + kWarps * 256 * 2 + 1024;
+constexpr size_t kChunkFixed = kCntWords * 4 + 3 * 1024;
 
 struct ChunkLayout {
-  size_t stage, permA, permB, win, whist, stack, total;
+  size_t stage, perm, out, cnt, stack, total;
 };
 
 __host__ __device__ inline ChunkLayout chunk_layout(u32 m, u32 RW) {
   ChunkLayout c;
   size_t o = 0;
   c.stage = o; o += (size_t)m * RW * 8;
-  c.permA = o; o += (size_t)m * 2;
-  c.permB = o; o += (size_t)m * 2;
-  c.win = o; o += (size_t)(m + 1) * 2 + 2;
+  c.perm = o; o += (size_t)m * 2;
+  c.out = o; o += (size_t)m * 2;
   o = (o + 15) & ~(size_t)15;
-  c.whist = o; o += (size_t)kWarps * 256 * 2;
+  c.cnt = o; o += (size_t)kCntWords * 4;
   c.stack = o; o += (size_t)(m / (kEsMax + 1) + 2) * 8;
   c.total = (o + 127) & ~(size_t)127;
   return c;
@@ -42,14 +47,13 @@ __host__ __device__ inline ChunkLayout chunk_layout(u32 m, u32 RW) {
 
 template <int KW, int RWT>
 struct ChunkCtx {
-  u64 km0, km1;   // key bits of words 0 and 1
+  u64 km0, km1;  // key bits of words 0 and 1
   u32 RW;
   const u64* stage;
-  u16* permA;
-  u16* permB;
-  u16* win;       // window digit of each position of the range being sorted
-  u16* whist;
-  u32* stack;  // pairs (begin, size)
+  u16* perm;     // the current order (record indices)
+  u16* out;      // scratch order
+  u32* cnt;      // 2^kIdxBits 16-bit counters, two per word
+  u32* stack;    // pairs (begin, size) of buckets still to sort
   u32 stack_cap;
 
   __device__ __forceinline__ Key<KW> key(u32 r) const {
@@ -59,151 +63,128 @@ struct ChunkCtx {
     if (KW == 2) k.w[KW - 1] = p[1] & km1;
     return k;
   }
+  __device__ __forceinline__ u32 count_of(u32 d) const { return (cnt[d >> 1] >> ((d & 1) * 16)) & 0xffffu; }
 };
 
-// Stable counting sort of positions [a, a + s) of `src` into `dst` by key bits [lo, lo + w).
+// Exclusive scan, in place, of nd (even, <= 2^kIdxBits) 16-bit counters packed two per word.
 template <int KW, int RWT>
-__device__ void lsd_pass(const ChunkCtx<KW, RWT>& c, const u16* src, u16* dst, u32 a, u32 s, u32 lo, u32 w) {
-  __shared__ u32 tcount[256];
-  __shared__ u32 scan_scr[kWarps + 1];
+__device__ void scan_counts(const ChunkCtx<KW, RWT>& c, u32 nd) {
+  __shared__ u32 scr[kWarps + 1];
   const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
-  const u32 nd = 1u << w;
-  for (u32 i = tid; i < (u32)kWarps * nd; i += kThreads) c.whist[i] = 0;
-  __syncthreads();
-  const u32 per_warp = ((s + kWarps * 32 - 1) / (kWarps * 32)) * 32;
-  const u32 items = per_warp / 32;
-  u16* wh = c.whist + warp * nd;
-  u32 packed[kChunkItems];
+  const u32 words = nd >> 1;
+  const u32 per = (words + kThreads - 1) / kThreads;
+  const u32 w0 = min(words, tid * per), w1 = min(words, w0 + per);
+  u32 sum = 0;
+  for (u32 w = w0; w < w1; w++) {
+    const u32 x = c.cnt[w];
+    sum += (x & 0xffffu) + (x >> 16);
+  }
+  u32 x = sum;
 #pragma unroll
-  for (int it = 0; it < kChunkItems; it++) {
-    packed[it] = 0xffffffffu;
-    if ((u32)it < items) {
-      const u32 pos = warp * per_warp + it * 32 + lane;
-      const bool valid = pos < s;
-      u32 d = 0;
-      if (valid) d = digit_of<KW>(c.key(src[a + pos]), lo, w);
-      const u32 peers = __match_any_sync(kFull, valid ? d : (0x10000u | lane));
-      const u32 before = __popc(peers & lanemask_lt());
-      u32 old = 0;
-      if (valid) old = wh[d];
-      __syncwarp();
-      if (valid && before == 0) wh[d] = (u16)(old + __popc(peers));
-      __syncwarp();
-      if (valid) packed[it] = (old + before) | (d << 16);
+  for (int o = 1; o < 32; o <<= 1) {
+    const u32 y = __shfl_up_sync(kFull, x, o);
+    if (lane >= o) x += y;
+  }
+  if (lane == 31) scr[warp] = x;
+  __syncthreads();
+  if (warp == 0) {
+    const u32 v = lane < kWarps ? scr[lane] : 0;
+    u32 t = v;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+      const u32 y = __shfl_up_sync(kFull, t, o);
+      if (lane >= o) t += y;
+    }
+    if (lane < kWarps) scr[lane] = t - v;
+  }
+  __syncthreads();
+  u32 run = scr[warp] + x - sum;
+  for (u32 w = w0; w < w1; w++) {
+    const u32 v = c.cnt[w];
+    const u32 lo = run, hi = run + (v & 0xffffu);
+    c.cnt[w] = lo | (hi << 16);
+    run = hi + (v >> 16);
+  }
+  __syncthreads();
+}
+
+// Distributes positions [a, a + s) of c.perm into c.out by a digit of the record (any order
+// inside a bucket); afterwards c.cnt holds every bucket's first position (relative to a).
+// by_index: the digit is the record's input position (unique); else key bits [lo, lo + w).
+template <int KW, int RWT>
+__device__ void distribute(const ChunkCtx<KW, RWT>& c, u32 a, u32 s, bool by_index, u32 lo, u32 w) {
+  const int tid = threadIdx.x;
+  const u32 nd = by_index ? (1u << kIdxBits) : (1u << w);
+  const u32 words = (nd + 1) >> 1;
+  for (u32 i = tid; i < words; i += kThreads) c.cnt[i] = 0;
+  __syncthreads();
+  u32 held[kChunkItems];
+#pragma unroll
+  for (int k = 0; k < kChunkItems; k++) {
+    const u32 i = tid + k * kThreads;
+    held[k] = 0xffffffffu;
+    if (i < s) {
+      const u32 r = c.perm[a + i];
+      const u32 d = by_index ? r : digit_of<KW>(c.key(r), lo, w);
+      const u32 old = atomicAdd(&c.cnt[d >> 1], 1u << ((d & 1) * 16));
+      held[k] = (((old >> ((d & 1) * 16)) & 0xffffu)) | (d << 16);
     }
   }
   __syncthreads();
-  for (u32 v = tid; v < nd; v += kThreads) {
-    u32 run = 0;
-    for (int q = 0; q < kWarps; q++) {
-      const u32 x = c.whist[q * nd + v];
-      c.whist[q * nd + v] = (u16)run;
-      run += x;
-    }
-    tcount[v] = run;
-  }
-  __syncthreads();
-  block_exclusive_scan(tcount, nd, scan_scr);
+  scan_counts(c, nd < 2 ? 2 : nd);
 #pragma unroll
-  for (int it = 0; it < kChunkItems; it++) {
-    if (packed[it] != 0xffffffffu) {
-      const u32 d = packed[it] >> 16;
-      const u32 pos = warp * per_warp + it * 32 + lane;
-      dst[a + tcount[d] + wh[d] + (packed[it] & 0xffffu)] = src[a + pos];
+  for (int k = 0; k < kChunkItems; k++) {
+    if (held[k] != 0xffffffffu) {
+      const u32 d = held[k] >> 16;
+      c.out[a + c.count_of(d) + (held[k] & 0xffffu)] = c.perm[a + tid + k * kThreads];
     }
   }
   __syncthreads();
 }
 
-// Sort positions [a, a + s) of permA by the full key, given that every key bit >= p is
-// shared by the range.  Runs longer than kEsMax go on the stack for another round.
+// Sorts positions [a, a + s) of c.perm by (key, input position), given that every key bit >= p
+// is shared by the range.  Buckets longer than kEsMax go on the stack.
 template <int KW, int RWT>
 __device__ void sort_round(const ChunkCtx<KW, RWT>& c, u32 a, u32 s, u32 p, u32* s_top) {
   const int tid = threadIdx.x;
-  const u32 lo1 = p > 16 ? p - 16 : 0;
-  const u32 wall = p - lo1;
-  const u32 wlo = wall > 8 ? wall - 8 : 0;
-  const u32 whi = wall - wlo;
-  if (wlo) {
-    lsd_pass(c, c.permA, c.permB, a, s, lo1, wlo);
-    lsd_pass(c, c.permB, c.permA, a, s, lo1 + wlo, whi);
-  } else {
-    lsd_pass(c, c.permA, c.permB, a, s, lo1, whi);
-    for (u32 i = tid; i < s; i += kThreads) c.permA[a + i] = c.permB[a + i];
-    __syncthreads();
-  }
-  // window digit (key bits [lo1, p)) of every position: non-decreasing along the range, so a
-  // run of equal digits is found by looking at neighbours and by binary search
-  u16* win = c.win;
-  for (u32 i = tid; i < s; i += kThreads) win[i] = (u16)digit_of<KW>(c.key(c.permA[a + i]), lo1, wall);
-  __syncthreads();
+  const u32 w = p > (u32)kWinBits ? (u32)kWinBits : p;
+  const u32 lo = p - w;
+  const u32 nd = 1u << w;
+  distribute(c, a, s, false, lo, w);
   for (u32 i = tid; i < s; i += kThreads) {
-    const u32 d = win[i];
-    const u32 r = c.permA[a + i];
-    const bool head = i == 0 || win[i - 1] != d;
-    const bool last = i + 1 == s || win[i + 1] != d;
-    if (head && last) {  // a run of one record
-      c.permB[a + i] = (u16)r;
-      continue;
-    }
-    // run start: first position with digit d in [i - kEsMax, i]
-    bool lng = false;
-    u32 st = i, en = i + 1;
-    const u32 L = i >= (u32)kEsMax ? i - kEsMax : 0;
-    if (i >= (u32)kEsMax && win[L] == d) {
-      lng = true;
+    const u32 r = c.out[a + i];
+    const Key<KW> kr = c.key(r);
+    const u32 d = digit_of<KW>(kr, lo, w);
+    const u32 st = c.count_of(d);
+    const u32 en = d + 1 < nd ? c.count_of(d + 1) : s;
+    const u32 sz = en - st;
+    if (sz == 1) {
+      c.perm[a + i] = (u16)r;
+    } else if (sz <= (u32)kEsMax) {
+      // enumeration sort: rank = records of the bucket that must precede this one
+      u32 rank = 0;
+      for (u32 q = st; q < en; q++) {
+        const u32 r2 = c.out[a + q];
+        const Key<KW> k2 = c.key(r2);
+        rank += key_less<KW>(k2, kr) || (key_eq<KW>(k2, kr) && r2 < r);
+      }
+      c.perm[a + st + rank] = (u16)r;
     } else {
-      u32 lo = L, hi = i;
-      while (lo < hi) {
-        const u32 mid = (lo + hi) >> 1;
-        if (win[mid] < d) lo = mid + 1; else hi = mid;
-      }
-      st = lo;
-      const u32 H = min(s - 1, i + kEsMax);
-      if (i + kEsMax < s && win[H] == d) {
-        lng = true;
-      } else {
-        u32 lo2 = i + 1, hi2 = H + 1;
-        while (lo2 < hi2) {
-          const u32 mid = (lo2 + hi2) >> 1;
-          if (win[mid] <= d) lo2 = mid + 1; else hi2 = mid;
-        }
-        en = lo2;
-        lng = en - st > (u32)kEsMax;
-      }
-    }
-    if (lng) {  // stays in place for now; its head measures it and pushes it
-      c.permB[a + i] = (u16)r;
-      if (head) {
-        u32 lo2 = i + 1, hi2 = s;
-        while (lo2 < hi2) {
-          const u32 mid = (lo2 + hi2) >> 1;
-          if (win[mid] <= d) lo2 = mid + 1; else hi2 = mid;
-        }
+      c.perm[a + i] = (u16)r;
+      if (i == st) {
         const u32 t = atomicAdd(s_top, 1u);
         if (t < c.stack_cap) {
-          c.stack[2 * t] = a + i;
-          c.stack[2 * t + 1] = lo2 - i;
+          c.stack[2 * t] = a + st;
+          c.stack[2 * t + 1] = sz;
         }
       }
-      continue;
     }
-    // enumeration sort: rank = records of the run that must precede this one
-    const Key<KW> kr = c.key(r);
-    u32 rank = 0;
-    for (u32 q = st; q < en; q++) {
-      const u32 r2 = c.permA[a + q];
-      const Key<KW> k2 = c.key(r2);
-      rank += key_less<KW>(k2, kr) || (key_eq<KW>(k2, kr) && r2 < r);
-    }
-    c.permB[a + st + rank] = (u16)r;
   }
-  __syncthreads();
-  for (u32 i = tid; i < s; i += kThreads) c.permA[a + i] = c.permB[a + i];
   __syncthreads();
 }
 
-// Highest differing key bit + 1 over positions [a, a + s) of permA (0: all keys equal).
+// Highest differing key bit + 1 over positions [a, a + s) (through c.perm, or the identity)
+// (0: all keys equal).
 template <int KW, int RWT>
 __device__ u32 range_top_bit(const ChunkCtx<KW, RWT>& c, u32 a, u32 s, bool through_perm) {
   __shared__ u64 red[kWarps][4];
@@ -211,7 +192,7 @@ __device__ u32 range_top_bit(const ChunkCtx<KW, RWT>& c, u32 a, u32 s, bool thro
   const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
   u64 kand[2] = {~0ull, ~0ull}, kor[2] = {0, 0};
   for (u32 i = tid; i < s; i += kThreads) {
-    const Key<KW> k = c.key(through_perm ? c.permA[a + i] : a + i);
+    const Key<KW> k = c.key(through_perm ? c.perm[a + i] : a + i);
 #pragma unroll
     for (int q = 0; q < KW; q++) {
       kand[q] &= k.w[q];
@@ -233,10 +214,10 @@ __device__ u32 range_top_bit(const ChunkCtx<KW, RWT>& c, u32 a, u32 s, bool thro
   __syncthreads();
   if (tid == 0) {
     u64 a2[2] = {~0ull, ~0ull}, o2[2] = {0, 0};
-    for (int w = 0; w < kWarps; w++)
+    for (int wq = 0; wq < kWarps; wq++)
       for (int q = 0; q < KW; q++) {
-        a2[q] &= red[w][q];
-        o2[q] |= red[w][2 + q];
+        a2[q] &= red[wq][q];
+        o2[q] |= red[wq][2 + q];
       }
     s_p = top_bit_plus1(a2[0] ^ o2[0], KW == 2 ? a2[1] ^ o2[1] : 0);
   }
@@ -261,10 +242,9 @@ __global__ void __launch_bounds__(kThreads, 2) k_chunk(Job j) {
   c.RW = RW;
   u64* stage = (u64*)(smem + lay.stage);
   c.stage = stage;
-  c.permA = (u16*)(smem + lay.permA);
-  c.permB = (u16*)(smem + lay.permB);
-  c.win = (u16*)(smem + lay.win);
-  c.whist = (u16*)(smem + lay.whist);
+  c.perm = (u16*)(smem + lay.perm);
+  c.out = (u16*)(smem + lay.out);
+  c.cnt = (u32*)(smem + lay.cnt);
   c.stack = (u32*)(smem + lay.stack);
   c.stack_cap = m / (kEsMax + 1) + 2;
   __shared__ u64 s_ticket;
@@ -294,7 +274,7 @@ __global__ void __launch_bounds__(kThreads, 2) k_chunk(Job j) {
       __syncthreads();
       continue;
     }
-    for (u32 i = tid; i < sz; i += kThreads) c.permA[i] = (u16)i;
+    for (u32 i = tid; i < sz; i += kThreads) c.perm[i] = (u16)i;
     if (tid == 0) s_top = 0;
     __syncthreads();
     sort_round(c, 0, sz, p, &s_top);
@@ -302,7 +282,7 @@ __global__ void __launch_bounds__(kThreads, 2) k_chunk(Job j) {
       __syncthreads();
       const u32 top = s_top;
       if (top == 0) break;
-      if (top > c.stack_cap) {  // cannot happen: runs on the stack are disjoint and > kEsMax
+      if (top > c.stack_cap) {  // cannot happen: buckets on the stack are disjoint and > kEsMax
         if (tid == 0) atomicOr(&ctl->err, kErrInternal);
         break;
       }
@@ -311,23 +291,29 @@ __global__ void __launch_bounds__(kThreads, 2) k_chunk(Job j) {
       if (tid == 0) s_top = top - 1;
       __syncthreads();
       const u32 pp = range_top_bit(c, a, s, true);
-      if (pp) sort_round(c, a, s, pp, &s_top);
+      if (pp) {
+        sort_round(c, a, s, pp, &s_top);
+      } else {  // all keys equal: back to input order
+        distribute(c, a, s, true, 0, 0);
+        for (u32 i = tid; i < s; i += kThreads) c.perm[a + i] = c.out[a + i];
+      }
     }
+    __syncthreads();
     // write the records in sorted order
     if (RW == 2) {
       for (u32 s = tid; s < sz; s += kThreads) {
-        const u32 r = c.permA[s];
+        const u32 r = c.perm[s];
         const ulonglong2 v = *reinterpret_cast<const ulonglong2*>(stage + 2 * (u64)r);
         __stcs(reinterpret_cast<ulonglong2*>(dst + 2 * (u64)s), v);
       }
     } else if (RWT != 0) {
       for (u32 q = tid; q < sz * RW; q += kThreads) {
         const u32 s = q / RW, w = q - s * RW;
-        __stcs(dst + q, stage[(u64)c.permA[s] * RW + w]);
+        __stcs(dst + q, stage[(u64)c.perm[s] * RW + w]);
       }
     } else {
       for (u32 s = tid; s < sz; s += kThreads) {
-        const u64* sp = stage + (u64)c.permA[s] * RW;
+        const u64* sp = stage + (u64)c.perm[s] * RW;
         for (u32 w = 0; w < RW; w++) __stcs(dst + (u64)s * RW + w, sp[w]);
       }
     }
@@ -413,12 +399,13 @@ int launch_copy(const Job& j, u32 grid, cudaStream_t s) {
 }
 
 // chunk_max for a record size: the largest range whose staging and index arrays fit the
-// shared memory of two CTAs per SM.
+// shared memory of two CTAs per SM (and whose positions fit kIdxBits bits).
 u32 chunk_capacity(u32 RW) {
   const size_t budget = kChunkSmem - kChunkFixed;
-  u32 m = (u32)(budget / (RW * 8 + 6));   // the record + three u16 index arrays
+  u32 m = (u32)(budget / (RW * 8 + 4));  // the record + two u16 index arrays
   m &= ~63u;
   if (m > (u32)kThreads * kChunkItems) m = kThreads * kChunkItems;
+  if (m > (1u << kIdxBits)) m = 1u << kIdxBits;
   return m;
 }
 

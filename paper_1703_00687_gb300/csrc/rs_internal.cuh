@@ -327,18 +327,21 @@ __device__ __forceinline__ void cp_async_wait_all() { asm volatile("cp.async.wai
 // Start copying `words` 8-byte words global -> shared (16-byte copies when the source is
 // 16-byte aligned; the destination always is).  Call cp_async_wait_all + __syncthreads
 // before reading them.
+// NT = threads of the calling CTA (all of them call it).
+template <int NT = kThreads>
 __device__ __forceinline__ void load_words_async(u64* dst, const u64* src, u64 words) {
   const int tid = threadIdx.x;
   if ((((uintptr_t)src) & 15) == 0) {
     const u64 pairs = words >> 1;
-    for (u64 i = tid; i < pairs; i += kThreads) cp_async16(dst + 2 * i, src + 2 * i);
+    for (u64 i = tid; i < pairs; i += NT) cp_async16(dst + 2 * i, src + 2 * i);
     if ((words & 1) && tid == 0) cp_async8(dst + words - 1, src + words - 1);
   } else {
-    for (u64 i = tid; i < words; i += kThreads) cp_async8(dst + i, src + i);
+    for (u64 i = tid; i < words; i += NT) cp_async8(dst + i, src + i);
   }
 }
 
-// Copy `words` 8-byte words global -> shared (coalesced, 16-byte loads when aligned).
+// Copy `words` 8-byte words global -> shared (coalesced, 16-byte loads when aligned), by a
+// CTA of kThreads threads.
 __device__ __forceinline__ void load_words(u64* dst, const u64* src, u64 words) {
   const int tid = threadIdx.x;
   if ((((uintptr_t)src) & 15) == 0) {
@@ -352,7 +355,7 @@ __device__ __forceinline__ void load_words(u64* dst, const u64* src, u64 words) 
   }
 }
 
-// Copy `words` words shared -> global.
+// Copy `words` words shared -> global, by a CTA of kThreads threads.
 __device__ __forceinline__ void store_words(u64* dst, const u64* src, u64 words) {
   const int tid = threadIdx.x;
   if ((((uintptr_t)dst) & 15) == 0) {

@@ -4,16 +4,19 @@
 // Then every sub-bin is classified: finished, sorted on chip (chunk), or large again.
 //
 // Kernels, all launched on the caller's stream:
-//   k_hist      histogram of each bin's digit (+ the bin's key AND/OR at level 0); the
-//               last CTA of a bin turns the counts into bucket bases.
-//   k_scatter   tile-wise stable scatter with a decoupled look-back across the tiles of a
-//               bin; also the key AND/OR of every sub-bin that stays large (digit skip).
-//   k_classify  sub-bin classification, chunk packing, next level's bin list.
+//   k_hist      histogram of each bin's digit, plus the AND/OR of the bin's keys.  The last
+//               CTA to count a bin checks that the digit starts at the bin's highest
+//               differing key bit (digits shared by every key are skipped, the paper's
+//               remark in section 1 that bins of equal keys do not shrink), flags a recount
+//               if not, marks a bin of equal keys finished, and turns counts into bases.
+//   k_scatter   tile-wise stable scatter with a decoupled look-back across the tiles of a bin.
+//   k_classify  sub-bin classification, chunk packing, the next level's bin list.
 #include "rs_internal.cuh"
 
 namespace rsg {
 
-// Exclusive scan of one u64 per thread; returns the exclusive prefix, total in *total.
+// Exclusive scan of one u64 per thread (kThreads threads); returns the exclusive prefix and
+// the total in *total.
 __device__ inline u64 block_scan_value64(u64 x, u64* scratch, u64* total) {
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
   u64 s = x;
@@ -42,7 +45,7 @@ __device__ inline u64 block_scan_value64(u64 x, u64* scratch, u64* total) {
 }
 
 // Tile numbering of bin list L: tile_start = exclusive prefix of ceil(size / T) in list order.
-// One CTA.
+// One CTA of kThreads threads.
 __device__ void finalize_list(const Job& j, int L) {
   __shared__ u64 scr[kWarps + 1];
   Ctl* ctl = j.ctl;
@@ -156,13 +159,17 @@ __global__ void __launch_bounds__(kThreads) k_init_segments(Job j) {
 __global__ void __launch_bounds__(kThreads) k_finalize0(Job j) { finalize_list(j, 0); }
 
 // ------------------------------------------------------------------- histogram
-constexpr int kHistItems = 8;  // records per thread per tile (T <= kThreads * kHistItems)
+constexpr int kHistCopies = 2;  // privatised histogram copies (by warp parity)
 
-// The last CTA to count a bin: at level 0 check that the digit starts at the bin's highest
-// differing key bit (else move it there and ask for a recount); then counts -> bases, and a
-// mask slot for every sub-bin that will need another pass.
+// mode 0: count + key AND/OR, then check the digit; mode 1: recount bins flagged kBinRedo;
+// mode 2: counts only (histogram entry point); mode 3: count + bases (given digit).
+//
+// The last CTA to count a bin finishes it: in mode 0, if every key is equal the bin is
+// finished as it is; if the digit does not start at the bin's highest differing bit, it is
+// moved there (never widened: the bin's pools were sized for W) and a recount is requested.
+// Otherwise the counts become exclusive bucket bases.
 template <int KW>
-__device__ void finish_bin(const Job& j, int L, u64 b, int level, int mode) {
+__device__ void finish_bin(const Job& j, int L, u64 b, int mode) {
   __shared__ u64 scr[kWarps + 1];
   __shared__ int s_ret;
   Ctl* ctl = j.ctl;
@@ -173,21 +180,25 @@ __device__ void finish_bin(const Job& j, int L, u64 b, int level, int mode) {
   u64* base = j.base[L] + bp->base_off;
   if (threadIdx.x == 0) {
     s_ret = 0;
-    if (level == 0 && mode == 0) {
+    if (mode == 0) {
       const u64 v0 = (__ldcg(&bp->kand[0]) ^ __ldcg(&bp->kor[0])) & j.keymask[0];
       const u64 v1 = KW == 2 ? (__ldcg(&bp->kand[1]) ^ __ldcg(&bp->kor[1])) & j.keymask[1] : 0;
       const u32 p = top_bit_plus1(v0, v1);
       if (p == 0) {
-        bp->flags |= kBinEqual;  // every key equal: already sorted, nothing to move
+        bp->flags |= kBinEqual;
         s_ret = 1;
       } else if (bp->lo + W != p) {
         u32 nlo, nW;
         plan_digit(size, p, j.chunk_max, j.wmax, &nlo, &nW);
-        if (nW > W) nW = W, nlo = p - W;
+        if (nW > W) {
+          nW = W;
+          nlo = p - W;
+        }
         bp->lo = nlo;
         bp->W = nW;
         bp->flags |= kBinRedo;
         bp->done = 0;
+        atomicAdd(&ctl->nredo, 1u);
         s_ret = 2;
       }
     }
@@ -205,50 +216,41 @@ __device__ void finish_bin(const Job& j, int L, u64 b, int level, int mode) {
   const u64 c1 = v0 + 1 < nd ? __ldcg(base + v0 + 1) : 0;
   u64 tot;
   const u64 ex = block_scan_value64(c0 + c1, scr, &tot);
-  const u64 nk = 2ull * KW;
-  for (int q = 0; q < 2; q++) {
-    const u32 v = v0 + q;
-    if (v >= nd) break;
-    const u64 c = q ? c1 : c0;
-    const u64 e = q ? ex + c0 : ex;
-    u64 tag = 0;
-    if (c > j.chunk_max) {
-      const u64 s = atomicAdd(&ctl->mslot_used, 1ull);
-      if (s < j.cap_mslots) {
-        u64* m = j.masks + s * nk;
-        for (int k = 0; k < KW; k++) {
-          m[k] = ~0ull;
-          m[KW + k] = 0;
-        }
-        tag = s + 1;
-      }
-    }
-    base[v] = e | (tag << kSlotShift);
-  }
+  if (v0 < nd) base[v0] = ex;
+  if (v0 + 1 < nd) base[v0 + 1] = ex + c0;
   if (mode == 1 && threadIdx.x == 0) bp->flags &= ~kBinRedo;
 }
 
-// mode 0: count (+ key AND/OR at level 0), finish bins; mode 1: recount level-0 bins flagged
-// kBinRedo; mode 2: counts only; mode 3: count and finish a bin whose digit is given.
+// Shared memory of k_hist: two buffers of a tile's keys (tile t+1 streams in while tile t
+// is counted).
+__host__ __device__ inline size_t hist_smem_bytes_for(u32 T, u32 KW) { return 2ull * T * KW * 8; }
+
+__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;\n" ::: "memory"); }
+__device__ __forceinline__ void cp_async_wait_one() { asm volatile("cp.async.wait_group 1;\n" ::: "memory"); }
+
 template <int KW>
-__global__ void __launch_bounds__(kThreads) k_hist(Job j, int level, int mode) {
+__global__ void __launch_bounds__(kThreads, 2) k_hist(Job j, int level, int mode) {
   const int L = level & 1;
   Ctl* ctl = j.ctl;
   const u64 nb = ctl->nbins[L];
   if (nb == 0) return;
+  if (mode == 1 && ctl->nredo == 0) return;
   const u64 ntiles = ctl->ntiles[L];
   Bin* bins = j.bins[L];
-  __shared__ u32 hist[1 << kWMax];
+  extern __shared__ __align__(16) unsigned char smem[];
+  u64* kbuf = (u64*)smem;  // [2][T][KW]
+  __shared__ u32 hist[kHistCopies << kWMax];
   __shared__ u64 red[kWarps][4];
   __shared__ int s_last;
   const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
-  const bool want_masks = level == 0 && mode == 0;
+  const bool want_masks = mode == 0;
+  const u32 T = j.T;
   const u64 per = ceil_div(ntiles, gridDim.x);
   const u64 t0 = blockIdx.x * per;
   const u64 t1 = min(ntiles, t0 + per);
   if (t0 >= t1) return;
-  for (u32 v = tid; v < (1u << kWMax); v += kThreads) hist[v] = 0;
-  u64 cur = find_bin(bins, nb, t0);
+  for (u32 v = tid; v < (kHistCopies << kWMax); v += kThreads) hist[v] = 0;
+  u32* my_hist = hist + ((warp & (kHistCopies - 1)) << kWMax);
   u32 counted = 0;
   u64 kand[2] = {~0ull, ~0ull}, kor[2] = {0ull, 0ull};
   __syncthreads();
@@ -259,9 +261,13 @@ __global__ void __launch_bounds__(kThreads) k_hist(Job j, int level, int mode) {
     const u32 nd = 1u << bb->W;
     const u64 bo = bb->base_off;
     for (u32 v = tid; v < nd; v += kThreads) {
-      const u32 h = hist[v];
+      u32 h = 0;
+#pragma unroll
+      for (int c = 0; c < kHistCopies; c++) {
+        h += hist[(c << kWMax) + v];
+        hist[(c << kWMax) + v] = 0;
+      }
       if (h) atomicAdd(&j.base[L][bo + v], (u64)h);
-      hist[v] = 0;
     }
     if (want_masks) {
 #pragma unroll
@@ -294,32 +300,36 @@ __global__ void __launch_bounds__(kThreads) k_hist(Job j, int level, int mode) {
     if (tid == 0) {
       __threadfence();
       const u32 old = atomicAdd(&bins[b].done, counted);
-      s_last = (u64)(old + counted) == ceil_div(bins[b].size, j.T);
+      s_last = (u64)(old + counted) == ceil_div(bins[b].size, (u64)T);
     }
     __syncthreads();
     if (s_last) {
       __threadfence();
-      finish_bin<KW>(j, L, b, level, mode);
+      finish_bin<KW>(j, L, b, mode);
     }
     __syncthreads();
     counted = 0;
   };
 
-  for (u64 t = t0; t < t1; t++) {
-    u64 b = cur;
-    while (b + 1 < nb && bins[b + 1].tile_start <= t) b++;
-    if (b != cur) {
-      if (counted) flush(cur);
-      cur = b;
-    }
-    const Bin* bp = &bins[b];
-    const u32 flags = bp->flags;
-    if (mode == 1 && !(flags & kBinRedo)) continue;
-    const u32 lo = bp->lo, W = bp->W, nd = 1u << W;
+  struct TileRef {
+    u64 b;
+    u32 cnt, lo, W, skip;
+  };
+  u64 walk = find_bin(bins, nb, t0);
+  // locate tile t, clear its look-back words, and start copying its keys into buffer `buf`
+  auto issue = [&](u64 t, int buf) {
+    while (walk + 1 < nb && bins[walk + 1].tile_start <= t) walk++;
+    const Bin* bp = &bins[walk];
+    TileRef tr;
+    tr.b = walk;
+    tr.skip = (mode == 1 && !(bp->flags & kBinRedo)) ? 1u : 0u;
+    tr.lo = bp->lo;
+    tr.W = bp->W;
     const u64 tib = t - bp->tile_start;
-    const u64 r0 = tib * j.T;
-    const u64 r1 = min(bp->size, r0 + j.T);
+    const u64 r0 = tib * T;
+    tr.cnt = (u32)min((u64)T, bp->size - r0);
     if (mode == 0 || mode == 3) {  // the scatter pass's look-back words of this tile start cleared
+      const u32 nd = 1u << tr.W;
       const u64 so = bp->status_off + tib * nd;
       if (j.wide) {
         u64* st = (u64*)j.status[L] + so;
@@ -329,63 +339,81 @@ __global__ void __launch_bounds__(kThreads) k_hist(Job j, int level, int mode) {
         for (u32 v = tid; v < nd; v += kThreads) st[v] = 0;
       }
     }
-    const u64* src = j.buf[bp->parity] + bp->begin * j.RW;
-    // all of the tile's key loads in flight before any is used
-    Key<KW> keys[kHistItems];
+    if (!tr.skip) {
+      const u64* src = j.buf[bp->parity] + (bp->begin + r0) * j.RW;
+      u64* dst = kbuf + (size_t)buf * T * KW;
+      for (u32 r = tid; r < tr.cnt; r += kThreads) {
+        if (KW == 2 && ((((uintptr_t)(src + (u64)r * j.RW)) & 15) == 0)) {
+          cp_async16(dst + 2 * r, src + (u64)r * j.RW);
+        } else {
 #pragma unroll
-    for (int it = 0; it < kHistItems; it++) {
-      const u64 r = r0 + (u64)it * kThreads + tid;
-      if (r < r1) keys[it] = load_key<KW>(src + r * j.RW, j);
+          for (int q = 0; q < KW; q++) cp_async8(dst + KW * r + q, src + (u64)r * j.RW + q);
+        }
+      }
     }
+    cp_async_commit();
+    return tr;
+  };
+
+  TileRef tn = issue(t0, 0);
+  u64 cur = tn.b;
+  for (u64 t = t0; t < t1; t++) {
+    const TileRef tc = tn;
+    const int buf = (int)((t - t0) & 1);
+    if (t + 1 < t1) tn = issue(t + 1, buf ^ 1);
+    else cp_async_commit();  // keep one group per iteration
+    cp_async_wait_one();     // tile t's keys have landed
+    __syncthreads();
+    if (tc.b != cur) {
+      if (counted) flush(cur);
+      cur = tc.b;
+    }
+    if (!tc.skip) {
+      const u64* kb = kbuf + (size_t)buf * T * KW;
+      for (u32 r = tid; r < tc.cnt; r += kThreads) {
+        Key<KW> k;
 #pragma unroll
-    for (int it = 0; it < kHistItems; it++) {
-      const u64 r = r0 + (u64)it * kThreads + tid;
-      if (r0 + (u64)it * kThreads >= r1) break;  // uniform
-      const bool valid = r < r1;
-      u32 d = 0;
-      if (valid) {
-        d = digit_of<KW>(keys[it], lo, W);
+        for (int q = 0; q < KW; q++) k.w[q] = kb[KW * r + q] & j.keymask[q];
+        atomicAdd(&my_hist[digit_of<KW>(k, tc.lo, tc.W)], 1u);
         if (want_masks) {
 #pragma unroll
           for (int q = 0; q < KW; q++) {
-            kand[q] &= keys[it].w[q];
-            kor[q] |= keys[it].w[q];
+            kand[q] &= k.w[q];
+            kor[q] |= k.w[q];
           }
         }
       }
-      const u32 peers = __match_any_sync(kFull, valid ? d : (0x10000u | lane));
-      if (valid && (peers & lanemask_lt()) == 0) atomicAdd(&hist[d], (u32)__popc(peers));
+      counted++;
     }
-    counted++;
+    __syncthreads();  // buffer `buf` is refilled by the next issue
   }
   if (counted) flush(cur);
 }
 
 // --------------------------------------------------------------------- scatter
-// Shared memory of k_scatter for digit width <= wmax and T records per tile.
+constexpr int kSThreads = 256;  // threads of a scatter CTA
+constexpr int kSWarps = kSThreads / 32;
+
+// Shared memory of k_scatter: T records, per-warp digit counters (row stride 2^wmax), the
+// tile's permutation, per-digit counts / run bases / global bases.
 struct ScatterLayout {
-  size_t stage, gbase, sand, sor, tcount, tbase, need, whist, perm, sdig, total;
+  size_t stage, whist, perm, tcount, tbase, gbase, total;
 };
 
-__host__ __device__ inline ScatterLayout scatter_layout(u32 T, u32 RW, u32 KW, u32 wmax) {
+__host__ __device__ inline ScatterLayout scatter_layout(u32 T, u32 RW, u32 wmax) {
   ScatterLayout s;
   const size_t nd = (size_t)1 << wmax;
   size_t o = 0;
   s.stage = o; o += (size_t)T * RW * 8;
-  s.gbase = o; o += nd * 8;
-  s.sand = o; o += nd * KW * 8;   // AND of the keys per digit, as 2*KW 32-bit halves
-  s.sor = o; o += nd * KW * 8;
+  s.whist = o; o += (size_t)kSWarps * nd * 4;
+  s.perm = o; o += (size_t)T * 2;
+  o = (o + 15) & ~(size_t)15;
   s.tcount = o; o += nd * 4;
   s.tbase = o; o += nd * 4;
-  s.need = o; o += (nd / 32 + 1) * 4;
-  s.whist = o; o += (size_t)kWarps * nd * 2;
-  s.perm = o; o += (size_t)T * 2;
-  s.sdig = o; o += (size_t)T * 2;
+  s.gbase = o; o += nd * 8;
   s.total = (o + 127) & ~(size_t)127;
   return s;
 }
-
-constexpr int kMaxItems = 8;  // records per thread per tile (T <= kThreads * kMaxItems)
 
 // Look-back word: 2-bit state (0 none, 1 tile count, 2 inclusive prefix) above the value.
 template <typename S>
@@ -401,6 +429,8 @@ struct LB<u64> {
   static constexpr u64 kVal = (1ull << 62) - 1;
 };
 
+// Publishes this tile's count of one digit and returns the number of records with that digit
+// in the bin's earlier tiles (decoupled look-back).  Every wait is bounded.
 template <typename S>
 __device__ __forceinline__ u64 look_back(S* st, u64 self, u32 nd, u64 tib, u32 c, const Job& j, bool stall) {
   Ctl* ctl = j.ctl;
@@ -417,8 +447,8 @@ __device__ __forceinline__ u64 look_back(S* st, u64 self, u32 nd, u64 tib, u32 c
     S w = wp ? ld_acquire(wp) : (S)ld_acquire(&ctl->never);
     u32 polls = 0;
     while ((w >> LB<S>::kShift) == 0) {
-      // bounded wait: give up after `watchdog` polls, or at once when any wait of this
-      // call has already given up (the result is then undefined and reported)
+      // give up after `watchdog` polls, or at once when any wait of this call has already
+      // given up (the result is then undefined and reported)
       if (++polls > j.watchdog || ((polls & 255) == 0 && (*(volatile u32*)&ctl->err & kErrTimeout))) {
         atomicOr(&ctl->err, kErrTimeout);
         break;
@@ -433,8 +463,9 @@ __device__ __forceinline__ u64 look_back(S* st, u64 self, u32 nd, u64 tib, u32 c
   return excl;
 }
 
-template <int KW, int RWT>
-__global__ void __launch_bounds__(kThreads) k_scatter(Job j, int level) {
+// IT = records per thread (T = kSThreads * IT).
+template <int KW, int RWT, int IT>
+__global__ void __launch_bounds__(kSThreads) k_scatter(Job j, int level) {
   const int L = level & 1;
   Ctl* ctl = j.ctl;
   const u64 nb = ctl->nbins[L];
@@ -442,46 +473,26 @@ __global__ void __launch_bounds__(kThreads) k_scatter(Job j, int level) {
   const u64 ntiles = ctl->ntiles[L];
   const Bin* bins = j.bins[L];
   const u32 RW = RWT ? (u32)RWT : j.RW;
-  const u32 T = j.T;
-  const ScatterLayout lay = scatter_layout(T, RW, KW, j.wmax);
+  constexpr u32 T = kSThreads * IT;
+  constexpr u32 PW = T / kSWarps;  // records per warp strip
+  const u32 WS = 1u << j.wmax;     // row stride of the per-warp counters
+  const ScatterLayout lay = scatter_layout(T, RW, j.wmax);
   extern __shared__ __align__(16) unsigned char smem[];
   u64* stage = (u64*)(smem + lay.stage);
-  u64* gbase = (u64*)(smem + lay.gbase);
-  u32* sand = (u32*)(smem + lay.sand);  // [v][2*KW] 32-bit halves: native shared atomics
-  u32* sor = (u32*)(smem + lay.sor);
+  u32* whist = (u32*)(smem + lay.whist);
+  u16* perm = (u16*)(smem + lay.perm);
   u32* tcount = (u32*)(smem + lay.tcount);
   u32* tbase = (u32*)(smem + lay.tbase);
-  u32* need = (u32*)(smem + lay.need);
-  u16* whist = (u16*)(smem + lay.whist);
-  u16* perm = (u16*)(smem + lay.perm);
-  u16* sdig = (u16*)(smem + lay.sdig);
+  u64* gbase = (u64*)(smem + lay.gbase);
   __shared__ u64 s_ticket, s_bin;
-  __shared__ u32 scan_scr[kWarps + 1];
+  __shared__ u32 scan_scr[kSWarps + 1];
   const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
-  const u32 its = T / kThreads;
-  const u32 per_warp = T / kWarps;
-  // Sub-bin key AND/OR accumulate in shared memory over all tiles this CTA takes from one
-  // bin, and go to global memory once per (CTA, bin).
-  u64 mask_bin = ~0ull;
-  auto flush_masks = [&](u64 mb) {
-    const Bin* mp = &bins[mb];
-    const u32 mnd = 1u << mp->W;
-    const u64* mbase = j.base[L] + mp->base_off;
-    for (u32 v = tid; v < mnd; v += kThreads) {
-      if (!((need[v >> 5] >> (v & 31)) & 1u)) continue;
-      const u64 slot = mbase[v] >> kSlotShift;
-      u64* m = j.masks + (slot - 1) * 2 * KW;
-#pragma unroll
-      for (int q = 0; q < KW; q++) {
-        const u64 a = ((u64)sand[v * 2 * KW + 2 * q + 1] << 32) | sand[v * 2 * KW + 2 * q];
-        const u64 o = ((u64)sor[v * 2 * KW + 2 * q + 1] << 32) | sor[v * 2 * KW + 2 * q];
-        if (o | ~a) {  // skip untouched entries
-          atomicAnd(&m[q], a);
-          atomicOr(&m[KW + q], o);
-        }
-      }
-    }
-  };
+  const u32 ltmask = lanemask_lt();
+  // per-warp counters: low half = this tile's count, high half = the warp's offset within
+  // the digit's run; the prefix pass rewrites each entry as (offset << 16), which also
+  // clears the count for the next tile
+  for (u32 i = tid; i < kSWarps * WS; i += kSThreads) whist[i] = 0;
+  u32* wh = whist + warp * WS;
 
   for (;;) {
     if (tid == 0) {
@@ -495,153 +506,132 @@ __global__ void __launch_bounds__(kThreads) k_scatter(Job j, int level) {
     __syncthreads();  // every thread has its ticket before thread 0 may take the next
     if (t >= ntiles) break;
     const Bin bin = bins[b];
-    const Bin* bp = &bin;
-    if (bp->flags & kBinEqual) continue;
-    const u32 lo = bp->lo, W = bp->W, nd = 1u << W;
-    const u64 tib = t - bp->tile_start;
+    if (bin.flags & kBinEqual) continue;
+    const u32 lo = bin.lo, W = bin.W, nd = 1u << W;
+    const u64 tib = t - bin.tile_start;
     const u64 r0 = tib * T;
-    const u32 cnt = (u32)min((u64)T, bp->size - r0);
-    const u64* src = j.buf[bp->parity] + (bp->begin + r0) * RW;
-    u64* dstb = j.buf[bp->parity ^ 1];
-    const u64* bbase = j.base[L] + bp->base_off;
+    const u32 cnt = (u32)min((u64)T, bin.size - r0);
+    const u64* src = j.buf[bin.parity] + (bin.begin + r0) * RW;
+    u64* dstb = j.buf[bin.parity ^ 1];
+    const u64* bbase = j.base[L] + bin.base_off;
 
-    load_words_async(stage, src, (u64)cnt * RW);
-    for (u32 i = tid; i < (u32)kWarps * nd; i += kThreads) whist[i] = 0;
-    if (b != mask_bin) {
-      if (mask_bin != ~0ull) flush_masks(mask_bin);
-      __syncthreads();
-      for (u32 i = tid; i < nd / 32 + 1; i += kThreads) need[i] = 0;
-      __syncthreads();
-      for (u32 v = tid; v < nd; v += kThreads) {
-        if (bbase[v] >> kSlotShift) {
-          atomicOr(&need[v >> 5], 1u << (v & 31));
-#pragma unroll
-          for (int k = 0; k < 2 * KW; k++) {
-            sand[v * 2 * KW + k] = ~0u;
-            sor[v * 2 * KW + k] = 0;
-          }
-        }
-      }
-      mask_bin = b;
-    }
+    load_words_async<kSThreads>(stage, src, (u64)cnt * RW);
     cp_async_wait_all();
     __syncthreads();
 
-    // stable rank: warp w owns records [w*per_warp, (w+1)*per_warp), visited in order
-    u32 packed[kMaxItems];
-    u16* wh = whist + warp * nd;
+    // stable rank: warp w owns records [w*PW, (w+1)*PW), visited in order
+    u32 packed[IT];
 #pragma unroll
-    for (int it = 0; it < kMaxItems; it++) {
-      packed[it] = 0xffffffffu;
-      if ((u32)it < its) {
-        const u32 r = warp * per_warp + it * 32 + lane;
-        const bool valid = r < cnt;
-        Key<KW> k;
-        u32 d = 0;
-        if (valid) {
-          k = load_key<KW>(stage + (u64)r * RW, j);
-          d = digit_of<KW>(k, lo, W);
-        }
-        const u32 peers = __match_any_sync(kFull, valid ? d : (0x10000u | lane));
-        const u32 before = __popc(peers & lanemask_lt());
-        u32 old = 0;
-        if (valid) old = wh[d];
-        __syncwarp();
-        if (valid && before == 0) wh[d] = (u16)(old + __popc(peers));
-        __syncwarp();
-        if (valid) {
-          packed[it] = (old + before) | (d << 16);
-          if ((need[d >> 5] >> (d & 31)) & 1u) {
-#pragma unroll
-            for (int q = 0; q < KW; q++) {
-              const u32 alo = __reduce_and_sync(peers, (u32)k.w[q]);
-              const u32 ahi = __reduce_and_sync(peers, (u32)(k.w[q] >> 32));
-              const u32 olo = __reduce_or_sync(peers, (u32)k.w[q]);
-              const u32 ohi = __reduce_or_sync(peers, (u32)(k.w[q] >> 32));
-              if (before == 0) {
-                atomicAnd(&sand[d * 2 * KW + 2 * q], alo);
-                atomicAnd(&sand[d * 2 * KW + 2 * q + 1], ahi);
-                atomicOr(&sor[d * 2 * KW + 2 * q], olo);
-                atomicOr(&sor[d * 2 * KW + 2 * q + 1], ohi);
-              }
-            }
-          }
-        }
-      }
+    for (int it = 0; it < IT; it++) {
+      const u32 r = warp * PW + it * 32 + lane;
+      const bool valid = r < cnt;
+      u32 d = 0;
+      if (valid) d = digit_of<KW>(load_key<KW>(stage + (u64)r * RW, j), lo, W);
+      const u32 peers = __match_any_sync(kFull, valid ? d : (0x10000u | lane));
+      const u32 before = __popc(peers & ltmask);
+      u32 old = 0;
+      if (valid) old = wh[d];
+      __syncwarp();
+      if (valid && before == 0) wh[d] = old + __popc(peers);
+      __syncwarp();
+      packed[it] = valid ? (((old & 0xffffu) + before) | (d << 16)) : 0xffffffffu;
     }
     __syncthreads();
-    // per digit: offsets of each warp's run, and the tile's count
-    for (u32 v = tid; v < nd; v += kThreads) {
+    for (u32 v = tid; v < nd; v += kSThreads) {
       u32 run = 0;
-      for (int w = 0; w < kWarps; w++) {
-        const u32 c = whist[w * nd + v];
-        whist[w * nd + v] = (u16)run;
-        run += c;
+#pragma unroll
+      for (int w = 0; w < kSWarps; w++) {
+        const u32 x = whist[w * WS + v];
+        whist[w * WS + v] = run << 16;
+        run += x & 0xffffu;
       }
       tcount[v] = run;
       tbase[v] = run;
     }
     __syncthreads();
-    block_exclusive_scan(tbase, nd, scan_scr);
-    // decoupled look-back over the earlier tiles of this bin: records of digit v before this tile
-    for (u32 v = tid; v < nd; v += kThreads) {
-      const u64 self = bp->status_off + tib * nd + v;
-      u64 excl;
+    block_exclusive_scan<kSThreads>(tbase, nd, scan_scr);
+    // decoupled look-back over the earlier tiles of this bin
+    for (u32 v = tid; v < nd; v += kSThreads) {
+      const u64 self = bin.status_off + tib * nd + v;
       const bool stall = j.inject && v == 0 && tib == 1;
-      if (j.wide)
-        excl = look_back<u64>((u64*)j.status[L], self, nd, tib, tcount[v], j, stall);
-      else
-        excl = look_back<u32>((u32*)j.status[L], self, nd, tib, tcount[v], j, stall);
-      gbase[v] = bp->begin + (bbase[v] & kBaseMask) + excl - tbase[v];
+      const u64 excl = j.wide ? look_back<u64>((u64*)j.status[L], self, nd, tib, tcount[v], j, stall)
+                              : look_back<u32>((u32*)j.status[L], self, nd, tib, tcount[v], j, stall);
+      gbase[v] = bin.begin + bbase[v] + excl - tbase[v];
     }
 #pragma unroll
-    for (int it = 0; it < kMaxItems; it++) {
+    for (int it = 0; it < IT; it++) {
       if (packed[it] != 0xffffffffu) {
         const u32 d = packed[it] >> 16;
-        const u32 slot = tbase[d] + whist[warp * nd + d] + (packed[it] & 0xffffu);
-        perm[slot] = (u16)(warp * per_warp + it * 32 + lane);
-        sdig[slot] = (u16)d;
+        perm[tbase[d] + (wh[d] >> 16) + (packed[it] & 0xffffu)] = (u16)(warp * PW + it * 32 + lane);
       }
     }
     __syncthreads();
     // write the tile in digit order: consecutive slots of one digit go to consecutive
     // records.  A destination outside the bin (possible only after a failed wait or a
     // corrupted histogram, both reported) is skipped, never written.
-    const u64 lo_rec = bp->begin, hi_rec = bp->begin + bp->size;
+    const u64 lo_rec = bin.begin, hi_rec = bin.begin + bin.size;
     bool bad = false;
     if (RW == 2) {
-      for (u32 s = tid; s < cnt; s += kThreads) {
+      for (u32 s = tid; s < cnt; s += kSThreads) {
         const u32 r = perm[s];
-        const u64 dst = gbase[sdig[s]] + s;
+        const ulonglong2 v = *reinterpret_cast<const ulonglong2*>(stage + 2 * r);
+        Key<KW> k;
+        k.w[0] = v.x & j.keymask[0];
+        if (KW == 2) k.w[KW - 1] = v.y & j.keymask[1];
+        const u64 dst = gbase[digit_of<KW>(k, lo, W)] + s;
         if (dst < lo_rec || dst >= hi_rec) { bad = true; continue; }
-        const ulonglong2 v = *reinterpret_cast<const ulonglong2*>(stage + 2 * (u64)r);
         __stcs(reinterpret_cast<ulonglong2*>(dstb + 2 * dst), v);
       }
-    } else if (RWT != 0) {
-      for (u32 q = tid; q < cnt * RW; q += kThreads) {
-        const u32 s = q / RW, w = q - s * RW;
-        const u32 r = perm[s];
-        const u64 dst = gbase[sdig[s]] + s;
-        if (dst < lo_rec || dst >= hi_rec) { bad = true; continue; }
-        __stcs(dstb + dst * RW + w, stage[(u64)r * RW + w]);
-      }
     } else {
-      for (u32 s = tid; s < cnt; s += kThreads) {
+      for (u32 s = tid; s < cnt; s += kSThreads) {
         const u32 r = perm[s];
-        const u64 dst = gbase[sdig[s]] + s;
+        const u64* sp = stage + (u64)r * RW;
+        const u64 dst = gbase[digit_of<KW>(load_key<KW>(sp, j), lo, W)] + s;
         if (dst < lo_rec || dst >= hi_rec) { bad = true; continue; }
         u64* d = dstb + dst * RW;
-        const u64* sp = stage + (u64)r * RW;
         for (u32 w = 0; w < RW; w++) __stcs(d + w, sp[w]);
       }
     }
     if (bad) atomicOr(&ctl->err, kErrInternal);
     __syncthreads();
   }
-  if (mask_bin != ~0ull) flush_masks(mask_bin);
 }
 
 // -------------------------------------------------------------------- classify
+// Highest differing key bit + 1 over 32 records spread over a sub-bin (the sample tells where
+// the sub-bin's next digit probably starts; the next histogram pass checks, and moves it).
+template <int KW>
+__device__ u32 sample_top_bit(const Job& j, const u64* rec, u64 c) {
+  u64 a[2] = {~0ull, ~0ull}, o[2] = {0, 0};
+  const int ns = 32;
+  for (int i = 0; i < ns; i++) {
+    const u64 r = (c * (u64)i) / ns;
+    const Key<KW> k = load_key<KW>(rec + r * j.RW, j);
+#pragma unroll
+    for (int q = 0; q < KW; q++) {
+      a[q] &= k.w[q];
+      o[q] |= k.w[q];
+    }
+  }
+  return top_bit_plus1(a[0] ^ o[0], KW == 2 ? a[1] ^ o[1] : 0);
+}
+
+__device__ void push_pieces(const Job& j, u64 begin, u64 c) {
+  Ctl* ctl = j.ctl;
+  const u64 np = ceil_div(c, kPieceRecords);
+  const u64 idx = atomicAdd(&ctl->npieces, np);
+  if (idx + np > j.cap_pieces) {
+    atomicOr(&ctl->err, kErrOverflow);
+    return;
+  }
+  for (u64 q = 0; q < np; q++) {
+    Piece pc;
+    pc.begin = begin + q * kPieceRecords;
+    pc.size = min(kPieceRecords, c - q * kPieceRecords);
+    j.pieces[idx + q] = pc;
+  }
+}
+
 template <int KW>
 __global__ void __launch_bounds__(kThreads) k_classify(Job j, int level) {
   const int L = level & 1, N = L ^ 1;
@@ -656,14 +646,16 @@ __global__ void __launch_bounds__(kThreads) k_classify(Job j, int level) {
   const int tid = threadIdx.x;
   for (u64 b = blockIdx.x; b < nb; b += gridDim.x) {
     const Bin bin = bins[b];
-    if (bin.flags & kBinEqual) continue;
+    if (bin.flags & kBinEqual) {  // finished without moving; copy back if it lives in tmp
+      if (tid == 0 && bin.parity) push_pieces(j, bin.begin, bin.size);
+      continue;
+    }
     const u32 nd = 1u << bin.W;
     const u32 p1 = bin.parity ^ 1;
     const u64* bbase = j.base[L] + bin.base_off;
     for (u32 v = tid; v < nd; v += kThreads) {
-      const u64 e = bbase[v];
-      u64 bv = e & kBaseMask;
-      u64 next = v + 1 < nd ? (bbase[v + 1] & kBaseMask) : bin.size;
+      u64 bv = bbase[v];
+      u64 next = v + 1 < nd ? bbase[v + 1] : bin.size;
       if (next < bv || next > bin.size) {  // inconsistent bases (only after a reported error)
         atomicOr(&ctl->err, kErrInternal);
         next = bv = min(bv, bin.size);
@@ -679,56 +671,34 @@ __global__ void __launch_bounds__(kThreads) k_classify(Job j, int level) {
       } else if (c <= j.chunk_max) {
         k = 2;
       } else {
-        const u64 slot = e >> kSlotShift;
-        u32 p = bin.lo;  // without masks: every bit below the digit may differ
-        bool equal = false;
-        if (slot) {
-          const u64* m = j.masks + (slot - 1) * 2 * KW;
-          const u64 v0 = (m[0] ^ m[KW]) & j.keymask[0];
-          const u64 v1 = KW == 2 ? (m[1] ^ m[KW + 1]) & j.keymask[1] : 0;
-          p = top_bit_plus1(v0, v1);
-          equal = p == 0;
-        }
+        k = 3;
         const u64 rb = bin.begin + bv;
-        if (equal) {
-          k = 4;
-          if (p1) {  // finished, but in tmp: copy back
-            const u64 np = ceil_div(c, kPieceRecords);
-            const u64 idx = atomicAdd(&ctl->npieces, np);
-            if (idx + np > j.cap_pieces) {
-              atomicOr(&ctl->err, kErrOverflow);
-            } else {
-              for (u64 q = 0; q < np; q++) {
-                Piece pc;
-                pc.begin = rb + q * kPieceRecords;
-                pc.size = min(kPieceRecords, c - q * kPieceRecords);
-                j.pieces[idx + q] = pc;
-              }
-            }
-          }
+        // every key bit >= bin.lo is shared by the sub-bin; guess where its next digit
+        // starts from a sample
+        u32 p = sample_top_bit<KW>(j, j.buf[p1] + rb * j.RW, c);
+        if (p == 0 || p > bin.lo) p = bin.lo;
+        if (p == 0) p = 1;
+        u32 nlo, nW;
+        plan_digit(c, p, j.chunk_max, j.wmax, &nlo, &nW);
+        const u32 nnd = 1u << nW;
+        const u64 tiles = ceil_div(c, j.T);
+        const u64 idx = atomicAdd(&ctl->nbins[N], 1ull);
+        const u64 bo = atomicAdd(&ctl->base_used[N], (u64)nnd);
+        const u64 so = atomicAdd(&ctl->status_used[N], tiles * nnd);
+        if (idx >= j.cap_bins || bo + nnd > j.cap_base || so + tiles * nnd > j.cap_status) {
+          atomicOr(&ctl->err, kErrOverflow);
         } else {
-          k = 3;
-          u32 nlo, nW;
-          plan_digit(c, p, j.chunk_max, j.wmax, &nlo, &nW);
-          const u32 nnd = 1u << nW;
-          const u64 tiles = ceil_div(c, j.T);
-          const u64 idx = atomicAdd(&ctl->nbins[N], 1ull);
-          const u64 bo = atomicAdd(&ctl->base_used[N], (u64)nnd);
-          const u64 so = atomicAdd(&ctl->status_used[N], tiles * nnd);
-          if (idx >= j.cap_bins || bo + nnd > j.cap_base || so + tiles * nnd > j.cap_status) {
-            atomicOr(&ctl->err, kErrOverflow);
-          } else {
-            Bin nbn = {};
-            nbn.begin = rb;
-            nbn.size = c;
-            nbn.base_off = bo;
-            nbn.status_off = so;
-            nbn.lo = nlo;
-            nbn.W = nW;
-            nbn.parity = p1;
-            j.bins[N][idx] = nbn;
-            for (u32 q = 0; q < nnd; q++) j.base[N][bo + q] = 0;
-          }
+          Bin nbn = {};
+          nbn.begin = rb;
+          nbn.size = c;
+          nbn.base_off = bo;
+          nbn.status_off = so;
+          nbn.kand[0] = nbn.kand[1] = ~0ull;
+          nbn.lo = nlo;
+          nbn.W = nW;
+          nbn.parity = p1;
+          j.bins[N][idx] = nbn;
+          for (u32 q = 0; q < nnd; q++) j.base[N][bo + q] = 0;
         }
       }
       cls[v] = k;
@@ -789,7 +759,7 @@ __global__ void __launch_bounds__(kThreads) k_classify(Job j, int level) {
     if (tid == 0) {
       ctl->s_ticket = 0;
       ctl->cls_done = 0;
-      ctl->mslot_used = 0;
+      ctl->nredo = 0;
       ctl->nbins[L] = 0;
       ctl->ntiles[L] = 0;
       ctl->base_used[L] = 0;
@@ -805,52 +775,63 @@ __global__ void k_read_counts(Job j, u64* out, u32 nd) {
 }
 
 // ------------------------------------------------------------------- launchers
-size_t scatter_smem_bytes(const Job& j) { return scatter_layout(j.T, j.RW, j.KW, j.wmax).total; }
+size_t scatter_smem_bytes(const Job& j) { return scatter_layout(j.T, j.RW, j.wmax).total; }
 
-template <int KW, int RWT>
-static void set_scatter_attr(const Job& j) {
-  cudaFuncSetAttribute(k_scatter<KW, RWT>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)scatter_smem_bytes(j));
-}
-
-template <int KW>
-static cudaError_t launch_scatter_kw(const Job& j, int level, u32 grid, cudaStream_t s) {
+template <int KW, int RWT, int IT>
+static cudaError_t launch_scatter_t(const Job& j, int level, u32 grid, cudaStream_t s, int* occ) {
   const size_t sm = scatter_smem_bytes(j);
-#define RS_SCAT(R)                                                                      \
-  do {                                                                                  \
-    cudaFuncSetAttribute(k_scatter<KW, R>, cudaFuncAttributeMaxDynamicSharedMemorySize, \
-                         (int)sm);                                                      \
-    k_scatter<KW, R><<<grid, kThreads, sm, s>>>(j, level);                             \
-  } while (0)
-  switch (j.RW) {
-    case 1: RS_SCAT(1); break;
-    case 2: RS_SCAT(2); break;
-    case 3: RS_SCAT(3); break;
-    case 4: RS_SCAT(4); break;
-    default: RS_SCAT(0); break;
+  cudaFuncSetAttribute(k_scatter<KW, RWT, IT>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
+  if (occ) {
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(occ, k_scatter<KW, RWT, IT>, kSThreads, sm) != cudaSuccess ||
+        *occ < 1)
+      *occ = 1;
+    return cudaSuccess;
   }
-#undef RS_SCAT
+  k_scatter<KW, RWT, IT><<<grid, kSThreads, sm, s>>>(j, level);
   return cudaGetLastError();
 }
 
-int scatter_ctas_per_sm(const Job& j, bool) {
-  int n = 0;
-  const size_t sm = scatter_smem_bytes(j);
-  cudaError_t e;
-  if (j.KW == 1) {
-    cudaFuncSetAttribute(k_scatter<1, 0>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
-    e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, k_scatter<1, 0>, kThreads, sm);
-  } else {
-    cudaFuncSetAttribute(k_scatter<2, 0>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
-    e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, k_scatter<2, 0>, kThreads, sm);
+template <int KW, int IT>
+static cudaError_t scatter_rw(const Job& j, int level, u32 grid, cudaStream_t s, int* occ) {
+  switch (j.RW) {
+    case 1: return launch_scatter_t<KW, 1, IT>(j, level, grid, s, occ);
+    case 2: return launch_scatter_t<KW, 2, IT>(j, level, grid, s, occ);
+    case 3: return launch_scatter_t<KW, 3, IT>(j, level, grid, s, occ);
+    case 4: return launch_scatter_t<KW, 4, IT>(j, level, grid, s, occ);
+    default: return launch_scatter_t<KW, 0, IT>(j, level, grid, s, occ);
   }
-  if (e != cudaSuccess || n < 1) n = 1;
+}
+
+template <int KW>
+static cudaError_t scatter_it(const Job& j, int level, u32 grid, cudaStream_t s, int* occ) {
+  switch (j.T / kSThreads) {
+    case 16: return scatter_rw<KW, 16>(j, level, grid, s, occ);
+    case 8: return scatter_rw<KW, 8>(j, level, grid, s, occ);
+    case 4: return scatter_rw<KW, 4>(j, level, grid, s, occ);
+    default: return scatter_rw<KW, 2>(j, level, grid, s, occ);
+  }
+}
+
+int scatter_ctas_per_sm(const Job& j, bool) {
+  int n = 1;
+  if (j.KW == 1) scatter_it<1>(j, 0, 0, 0, &n);
+  else scatter_it<2>(j, 0, 0, 0, &n);
   return n;
 }
 
+static size_t hist_smem(const Job& j) { return hist_smem_bytes_for(j.T, j.KW); }
+
 int hist_ctas_per_sm(const Job& j) {
   int n = 0;
-  cudaError_t e = j.KW == 1 ? cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, k_hist<1>, kThreads, 0)
-                            : cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, k_hist<2>, kThreads, 0);
+  const size_t sm = hist_smem(j);
+  cudaError_t e;
+  if (j.KW == 1) {
+    cudaFuncSetAttribute(k_hist<1>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
+    e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, k_hist<1>, kThreads, sm);
+  } else {
+    cudaFuncSetAttribute(k_hist<2>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
+    e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, k_hist<2>, kThreads, sm);
+  }
   if (e != cudaSuccess || n < 1) n = 1;
   return n;
 }
@@ -875,13 +856,19 @@ int launch_init_segments(const Job& j, u32 grid, cudaStream_t s) {
 }
 
 int launch_hist(const Job& j, int level, int mode, u32 grid, cudaStream_t s) {
-  if (j.KW == 1) k_hist<1><<<grid, kThreads, 0, s>>>(j, level, mode);
-  else k_hist<2><<<grid, kThreads, 0, s>>>(j, level, mode);
+  const size_t sm = hist_smem(j);
+  if (j.KW == 1) {
+    cudaFuncSetAttribute(k_hist<1>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
+    k_hist<1><<<grid, kThreads, sm, s>>>(j, level, mode);
+  } else {
+    cudaFuncSetAttribute(k_hist<2>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
+    k_hist<2><<<grid, kThreads, sm, s>>>(j, level, mode);
+  }
   return cudaGetLastError() == cudaSuccess ? 1 : -1;
 }
 
 int launch_scatter(const Job& j, int level, bool, u32 grid, cudaStream_t s) {
-  cudaError_t e = j.KW == 1 ? launch_scatter_kw<1>(j, level, grid, s) : launch_scatter_kw<2>(j, level, grid, s);
+  cudaError_t e = j.KW == 1 ? scatter_it<1>(j, level, grid, s, nullptr) : scatter_it<2>(j, level, grid, s, nullptr);
   return e == cudaSuccess ? 1 : -1;
 }
 

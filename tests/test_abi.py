@@ -82,6 +82,8 @@ def test_plan_validation_and_roundtrip():
         rg.set_plan(digit_bits_max=12)
     with pytest.raises(rg.RadixSortError):
         rg.set_plan(tile_records=700)
+    with pytest.raises(rg.RadixSortError):
+        rg.set_plan(tile_records=1536)
     rg.set_plan(digit_bits_max=10, tile_records=2048, chunk_records=1000)
     assert rg.get_plan()["tile_records"] == 2048
     rg.set_plan(**old)

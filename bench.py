@@ -54,6 +54,7 @@ def parse():
     p.add_argument("--no-cpu", action="store_true")
     p.add_argument("--cpu-seconds", type=float, default=12.0, help="CPU oracle sample budget")
     p.add_argument("--profile-out", default=None, help="write per-kernel timing records here (json)")
+    p.add_argument("--plan", default="", help="tuning knobs, e.g. digit_bits_max=9,tile_records=2048")
     return p.parse_args()
 
 
@@ -215,6 +216,9 @@ def main():
     kind, n, R, K, seed, desc = WORKLOADS[args.workload]
     if args.n:
         n = args.n
+    if args.plan:
+        knobs = dict(kv.split("=") for kv in args.plan.split(","))
+        rg.set_plan(**{k: int(v) for k, v in knobs.items()})
     seed = seed + 1000 * rank  # every replica sorts its own data
     # input: generated on the host (pinned), one resident pristine copy on the device
     h_in = torch.empty((n, R), dtype=torch.uint8, pin_memory=True)
@@ -326,7 +330,7 @@ def main():
             "warmup": args.warmup, "ms_per_step": tot_ms / args.steps, "higher_is_better": True, "scaling": "weak",
             "vs_baseline": None, "dtype": "u64", "data": "synthetic",
             "config": {"workload": args.workload, "n": n, "rec_size": R, "key_size": K, "keys": desc,
-                       "seed": seed, "parallelism": f"replicas{world}",
+                       "seed": seed, "parallelism": f"replicas{world}", "plan": rg.get_plan(),
                        "l2": "input 16 GB >> L2; pristine input restored into the sort buffer before every step"},
             "roofline": roof, "hbm": hbm, "kernels": per, "gpu_launches": launches, "clocks": clk.summary(),
             "e2e": e2e, "cpu_baseline": cpu, "step_ms": step_ms,

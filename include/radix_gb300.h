@@ -126,7 +126,7 @@ rs_status radix_sort_release(void);
  */
 typedef struct rs_plan {
   uint32_t digit_bits_max;  /* widest digit of a distribution pass: 8..10 */
-  uint32_t tile_records;    /* records per distribution tile: 512, 1024, 2048 or 4096 */
+  uint32_t tile_records;    /* records per distribution tile: 256, 512, 1024, 2048 or 4096 */
   uint32_t chunk_records;   /* largest bin sorted on chip: 64.. the shared-memory maximum */
   uint32_t sm_limit;        /* use at most this many SMs for the persistent grids */
   uint32_t watchdog_polls;  /* polls of a look-back wait before it gives up */

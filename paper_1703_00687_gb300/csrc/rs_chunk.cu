@@ -19,14 +19,16 @@
 
 namespace rsg {
 
+constexpr int kCThreads = 1024;  // threads of a chunk CTA (one CTA per SM)
+constexpr int kCWarps = kCThreads / 32;
 constexpr int kEsMax = 48;       // largest bucket finished by enumeration sort
 constexpr int kWinBits = 12;     // digit of the on-chip distribution pass
 constexpr int kIdxBits = 13;     // input positions of a chunk (chunk_max <= 2^13)
-constexpr int kChunkItems = 12;  // positions per thread (chunk_max <= 512 * 12)
+constexpr int kChunkItems = 8;   // positions per thread (chunk_max <= 1024 * 8)
 constexpr int kCntWords = 1 << (kIdxBits - 1);  // two 16-bit counters per word
-// per-CTA shared memory the chunk kernel may use (two CTAs per SM), and what is not per record
-constexpr size_t kChunkSmem = 112 * 1024;
-constexpr size_t kChunkFixed = kCntWords * 4 + 3 * 1024;
+// shared memory of the chunk CTA, and the part that is not per record
+constexpr size_t kChunkSmem = 220 * 1024;
+constexpr size_t kChunkFixed = kCntWords * 4 + 4 * 1024;
 
 struct ChunkLayout {
   size_t stage, perm, out, cnt, stack, total;
@@ -35,7 +37,7 @@ struct ChunkLayout {
 __host__ __device__ inline ChunkLayout chunk_layout(u32 m, u32 RW) {
   ChunkLayout c;
   size_t o = 0;
-  c.stage = o; o += (size_t)m * RW * 8;
+  c.stage = o; o += 2 * (size_t)m * RW * 8;  // two stage buffers: the next chunk streams in
   c.perm = o; o += (size_t)m * 2;
   c.out = o; o += (size_t)m * 2;
   o = (o + 15) & ~(size_t)15;
@@ -69,10 +71,10 @@ struct ChunkCtx {
 // Exclusive scan, in place, of nd (even, <= 2^kIdxBits) 16-bit counters packed two per word.
 template <int KW, int RWT>
 __device__ void scan_counts(const ChunkCtx<KW, RWT>& c, u32 nd) {
-  __shared__ u32 scr[kWarps + 1];
+  __shared__ u32 scr[kCWarps + 1];
   const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
   const u32 words = nd >> 1;
-  const u32 per = (words + kThreads - 1) / kThreads;
+  const u32 per = (words + kCThreads - 1) / kCThreads;
   const u32 w0 = min(words, tid * per), w1 = min(words, w0 + per);
   u32 sum = 0;
   for (u32 w = w0; w < w1; w++) {
@@ -88,14 +90,14 @@ __device__ void scan_counts(const ChunkCtx<KW, RWT>& c, u32 nd) {
   if (lane == 31) scr[warp] = x;
   __syncthreads();
   if (warp == 0) {
-    const u32 v = lane < kWarps ? scr[lane] : 0;
+    const u32 v = lane < kCWarps ? scr[lane] : 0;
     u32 t = v;
 #pragma unroll
     for (int o = 1; o < 32; o <<= 1) {
       const u32 y = __shfl_up_sync(kFull, t, o);
       if (lane >= o) t += y;
     }
-    if (lane < kWarps) scr[lane] = t - v;
+    if (lane < kCWarps) scr[lane] = t - v;
   }
   __syncthreads();
   u32 run = scr[warp] + x - sum;
@@ -111,20 +113,22 @@ __device__ void scan_counts(const ChunkCtx<KW, RWT>& c, u32 nd) {
 // Distributes positions [a, a + s) of c.perm into c.out by a digit of the record (any order
 // inside a bucket); afterwards c.cnt holds every bucket's first position (relative to a).
 // by_index: the digit is the record's input position (unique); else key bits [lo, lo + w).
+// identity: c.perm is the identity over the range (not read).
 template <int KW, int RWT>
-__device__ void distribute(const ChunkCtx<KW, RWT>& c, u32 a, u32 s, bool by_index, u32 lo, u32 w) {
+__device__ void distribute(const ChunkCtx<KW, RWT>& c, u32 a, u32 s, bool by_index, u32 lo, u32 w,
+                           bool identity = false) {
   const int tid = threadIdx.x;
   const u32 nd = by_index ? (1u << kIdxBits) : (1u << w);
   const u32 words = (nd + 1) >> 1;
-  for (u32 i = tid; i < words; i += kThreads) c.cnt[i] = 0;
+  for (u32 i = tid; i < words; i += kCThreads) c.cnt[i] = 0;
   __syncthreads();
   u32 held[kChunkItems];
 #pragma unroll
   for (int k = 0; k < kChunkItems; k++) {
-    const u32 i = tid + k * kThreads;
+    const u32 i = tid + k * kCThreads;
     held[k] = 0xffffffffu;
     if (i < s) {
-      const u32 r = c.perm[a + i];
+      const u32 r = identity ? a + i : c.perm[a + i];
       const u32 d = by_index ? r : digit_of<KW>(c.key(r), lo, w);
       const u32 old = atomicAdd(&c.cnt[d >> 1], 1u << ((d & 1) * 16));
       held[k] = (((old >> ((d & 1) * 16)) & 0xffffu)) | (d << 16);
@@ -136,7 +140,8 @@ __device__ void distribute(const ChunkCtx<KW, RWT>& c, u32 a, u32 s, bool by_ind
   for (int k = 0; k < kChunkItems; k++) {
     if (held[k] != 0xffffffffu) {
       const u32 d = held[k] >> 16;
-      c.out[a + c.count_of(d) + (held[k] & 0xffffu)] = c.perm[a + tid + k * kThreads];
+      const u32 i = tid + k * kCThreads;
+      c.out[a + c.count_of(d) + (held[k] & 0xffffu)] = identity ? (u16)(a + i) : c.perm[a + i];
     }
   }
   __syncthreads();
@@ -145,13 +150,13 @@ __device__ void distribute(const ChunkCtx<KW, RWT>& c, u32 a, u32 s, bool by_ind
 // Sorts positions [a, a + s) of c.perm by (key, input position), given that every key bit >= p
 // is shared by the range.  Buckets longer than kEsMax go on the stack.
 template <int KW, int RWT>
-__device__ void sort_round(const ChunkCtx<KW, RWT>& c, u32 a, u32 s, u32 p, u32* s_top) {
+__device__ void sort_round(const ChunkCtx<KW, RWT>& c, u32 a, u32 s, u32 p, u32* s_top, bool identity = false) {
   const int tid = threadIdx.x;
   const u32 w = p > (u32)kWinBits ? (u32)kWinBits : p;
   const u32 lo = p - w;
   const u32 nd = 1u << w;
-  distribute(c, a, s, false, lo, w);
-  for (u32 i = tid; i < s; i += kThreads) {
+  distribute(c, a, s, false, lo, w, identity);
+  for (u32 i = tid; i < s; i += kCThreads) {
     const u32 r = c.out[a + i];
     const Key<KW> kr = c.key(r);
     const u32 d = digit_of<KW>(kr, lo, w);
@@ -187,11 +192,11 @@ __device__ void sort_round(const ChunkCtx<KW, RWT>& c, u32 a, u32 s, u32 p, u32*
 // (0: all keys equal).
 template <int KW, int RWT>
 __device__ u32 range_top_bit(const ChunkCtx<KW, RWT>& c, u32 a, u32 s, bool through_perm) {
-  __shared__ u64 red[kWarps][4];
+  __shared__ u64 red[kCWarps][4];
   __shared__ u32 s_p;
   const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
   u64 kand[2] = {~0ull, ~0ull}, kor[2] = {0, 0};
-  for (u32 i = tid; i < s; i += kThreads) {
+  for (u32 i = tid; i < s; i += kCThreads) {
     const Key<KW> k = c.key(through_perm ? c.perm[a + i] : a + i);
 #pragma unroll
     for (int q = 0; q < KW; q++) {
@@ -214,7 +219,7 @@ __device__ u32 range_top_bit(const ChunkCtx<KW, RWT>& c, u32 a, u32 s, bool thro
   __syncthreads();
   if (tid == 0) {
     u64 a2[2] = {~0ull, ~0ull}, o2[2] = {0, 0};
-    for (int wq = 0; wq < kWarps; wq++)
+    for (int wq = 0; wq < kCWarps; wq++)
       for (int q = 0; q < KW; q++) {
         a2[q] &= red[wq][q];
         o2[q] |= red[wq][2 + q];
@@ -227,8 +232,10 @@ __device__ u32 range_top_bit(const ChunkCtx<KW, RWT>& c, u32 a, u32 s, bool thro
   return p;
 }
 
+// One CTA per SM: while a chunk is sorted, the next chunk's records stream into the other
+// stage buffer.
 template <int KW, int RWT>
-__global__ void __launch_bounds__(kThreads, 2) k_chunk(Job j) {
+__global__ void __launch_bounds__(kCThreads, 1) k_chunk(Job j) {
   Ctl* ctl = j.ctl;
   const u64 nch = ctl->nchunks;
   if (nch == 0) return;
@@ -240,85 +247,113 @@ __global__ void __launch_bounds__(kThreads, 2) k_chunk(Job j) {
   c.km0 = j.keymask[0];
   c.km1 = j.keymask[1];
   c.RW = RW;
-  u64* stage = (u64*)(smem + lay.stage);
-  c.stage = stage;
+  u64* stage0 = (u64*)(smem + lay.stage);
   c.perm = (u16*)(smem + lay.perm);
   c.out = (u16*)(smem + lay.out);
   c.cnt = (u32*)(smem + lay.cnt);
   c.stack = (u32*)(smem + lay.stack);
   c.stack_cap = m / (kEsMax + 1) + 2;
-  __shared__ u64 s_ticket;
+  __shared__ Chunk s_ch[2];
+  __shared__ u64 s_t[2];
   __shared__ u32 s_top;
   const int tid = threadIdx.x;
-  for (;;) {
-    if (tid == 0) s_ticket = atomicAdd(&ctl->chunk_ticket, 1ull);
-    __syncthreads();
-    const u64 t = s_ticket;
-    __syncthreads();  // every thread has its ticket before thread 0 may take the next
-    if (t >= nch) break;
-    const Chunk ch = j.chunks[t];
-    const u32 sz = ch.size;
-    if (sz > m || ch.begin > j.n || ch.begin + sz > j.n) {  // never produced; reported, not touched
-      if (tid == 0) atomicOr(&ctl->err, kErrInternal);
-      continue;
-    }
-    const u64* src = j.buf[(ch.flags & kChSrcTmp) ? 1 : 0] + ch.begin * RW;
-    u64* dst = j.buf[0] + ch.begin * RW;
-    load_words_async(stage, src, (u64)sz * RW);
-    cp_async_wait_all();
-    __syncthreads();
-    u32 p = 0;
-    if (!(ch.flags & kChCopyOnly)) p = range_top_bit(c, 0, sz, false);
-    if (p == 0) {  // already in order
-      if (src != dst) store_words(dst, stage, (u64)sz * RW);
-      __syncthreads();
-      continue;
-    }
-    for (u32 i = tid; i < sz; i += kThreads) c.perm[i] = (u16)i;
-    if (tid == 0) s_top = 0;
-    __syncthreads();
-    sort_round(c, 0, sz, p, &s_top);
-    for (;;) {
-      __syncthreads();
-      const u32 top = s_top;
-      if (top == 0) break;
-      if (top > c.stack_cap) {  // cannot happen: buckets on the stack are disjoint and > kEsMax
-        if (tid == 0) atomicOr(&ctl->err, kErrInternal);
-        break;
-      }
-      const u32 a = c.stack[2 * (top - 1)], s = c.stack[2 * (top - 1) + 1];
-      __syncthreads();
-      if (tid == 0) s_top = top - 1;
-      __syncthreads();
-      const u32 pp = range_top_bit(c, a, s, true);
-      if (pp) {
-        sort_round(c, a, s, pp, &s_top);
-      } else {  // all keys equal: back to input order
-        distribute(c, a, s, true, 0, 0);
-        for (u32 i = tid; i < s; i += kThreads) c.perm[a + i] = c.out[a + i];
+
+  // thread 0: take a ticket and read its chunk (an unusable descriptor is reported, not used)
+  auto fetch = [&](int slot, u64 t) {
+    Chunk ch = {};
+    if (t < nch) {
+      ch = j.chunks[t];
+      if (ch.size > m || ch.begin > j.n || ch.begin + ch.size > j.n) {
+        atomicOr(&ctl->err, kErrInternal);
+        ch.size = 0;
       }
     }
-    __syncthreads();
-    // write the records in sorted order
-    if (RW == 2) {
-      for (u32 s = tid; s < sz; s += kThreads) {
-        const u32 r = c.perm[s];
-        const ulonglong2 v = *reinterpret_cast<const ulonglong2*>(stage + 2 * (u64)r);
-        __stcs(reinterpret_cast<ulonglong2*>(dst + 2 * (u64)s), v);
-      }
-    } else if (RWT != 0) {
-      for (u32 q = tid; q < sz * RW; q += kThreads) {
-        const u32 s = q / RW, w = q - s * RW;
-        __stcs(dst + q, stage[(u64)c.perm[s] * RW + w]);
-      }
-    } else {
-      for (u32 s = tid; s < sz; s += kThreads) {
-        const u64* sp = stage + (u64)c.perm[s] * RW;
-        for (u32 w = 0; w < RW; w++) __stcs(dst + (u64)s * RW + w, sp[w]);
-      }
-    }
-    __syncthreads();
+    s_ch[slot] = ch;
+    s_t[slot] = t;
+  };
+  auto issue = [&](int slot) {
+    const Chunk& ch = s_ch[slot];
+    if (s_t[slot] < nch && ch.size)
+      load_words_async<kCThreads>(stage0 + (size_t)slot * m * RW,
+                                  j.buf[(ch.flags & kChSrcTmp) ? 1 : 0] + ch.begin * RW, (u64)ch.size * RW);
+    cp_async_commit();
+  };
+
+  if (tid == 0) {
+    fetch(0, atomicAdd(&ctl->chunk_ticket, 1ull));
+    fetch(1, atomicAdd(&ctl->chunk_ticket, 1ull));
   }
+  __syncthreads();
+  issue(0);
+  issue(1);
+  int cur = 0;
+  for (;;) {
+    cp_async_wait_one();
+    __syncthreads();
+    if (s_t[cur] >= nch) break;  // tickets are taken in order: no later chunk either
+    const Chunk ch = s_ch[cur];
+    u64 nt = 0;
+    if (tid == 0) nt = atomicAdd(&ctl->chunk_ticket, 1ull);  // used at the end of this chunk
+    const u32 sz = ch.size;
+    c.stage = stage0 + (size_t)cur * m * RW;
+    const u64* stage = c.stage;
+    u64* dst = j.buf[0] + ch.begin * RW;
+    const bool in_place = !(ch.flags & kChSrcTmp);
+    u32 p = 0;
+    if (sz && !(ch.flags & kChCopyOnly)) p = ch.p ? ch.p : range_top_bit(c, 0, sz, false);
+    if (sz && p) {
+      if (tid == 0) s_top = 0;
+      sort_round(c, 0, sz, p, &s_top, true);
+      for (;;) {
+        __syncthreads();
+        const u32 top = s_top;
+        if (top == 0) break;
+        if (top > c.stack_cap) {  // cannot happen: buckets on the stack are disjoint and > kEsMax
+          if (tid == 0) atomicOr(&ctl->err, kErrInternal);
+          break;
+        }
+        const u32 a = c.stack[2 * (top - 1)], s = c.stack[2 * (top - 1) + 1];
+        __syncthreads();
+        if (tid == 0) s_top = top - 1;
+        __syncthreads();
+        const u32 pp = range_top_bit(c, a, s, true);
+        if (pp) {
+          sort_round(c, a, s, pp, &s_top);
+        } else {  // all keys equal: back to input order
+          distribute(c, a, s, true, 0, 0);
+          for (u32 i = tid; i < s; i += kCThreads) c.perm[a + i] = c.out[a + i];
+        }
+      }
+      __syncthreads();
+      // write the records in sorted order
+      if (RW == 2) {
+        for (u32 s = tid; s < sz; s += kCThreads) {
+          const u32 r = c.perm[s];
+          const ulonglong2 v = *reinterpret_cast<const ulonglong2*>(stage + 2 * (u64)r);
+          __stcs(reinterpret_cast<ulonglong2*>(dst + 2 * (u64)s), v);
+        }
+      } else if (RWT != 0) {
+        for (u32 q = tid; q < sz * RW; q += kCThreads) {
+          const u32 s = q / RW, w = q - s * RW;
+          __stcs(dst + q, stage[(u64)c.perm[s] * RW + w]);
+        }
+      } else {
+        for (u32 s = tid; s < sz; s += kCThreads) {
+          const u64* sp = stage + (u64)c.perm[s] * RW;
+          for (u32 w = 0; w < RW; w++) __stcs(dst + (u64)s * RW + w, sp[w]);
+        }
+      }
+    } else if (sz && !in_place) {  // already in order, but in tmp
+      const u64 words = (u64)sz * RW;
+      for (u64 i = tid; i < words; i += kCThreads) __stcs(dst + i, stage[i]);
+    }
+    __syncthreads();  // stage buffer `cur` is free
+    if (tid == 0) fetch(cur, nt);
+    __syncthreads();
+    issue(cur);
+    cur ^= 1;
+  }
+  cp_async_wait_all();
 }
 
 // Finished ranges that live in tmp: copy to in.
@@ -360,7 +395,7 @@ static cudaError_t launch_chunks_kw(const Job& j, u32 grid, cudaStream_t s) {
   do {                                                                               \
     cudaFuncSetAttribute(k_chunk<KW, R>, cudaFuncAttributeMaxDynamicSharedMemorySize, \
                          (int)sm);                                                   \
-    k_chunk<KW, R><<<grid, kThreads, sm, s>>>(j);                                   \
+    k_chunk<KW, R><<<grid, kCThreads, sm, s>>>(j);                                  \
   } while (0)
   switch (j.RW) {
     case 1: RS_CH(1); break;
@@ -379,10 +414,10 @@ int chunk_ctas_per_sm(const Job& j) {
   cudaError_t e;
   if (j.KW == 1) {
     cudaFuncSetAttribute(k_chunk<1, 0>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
-    e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, k_chunk<1, 0>, kThreads, sm);
+    e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, k_chunk<1, 0>, kCThreads, sm);
   } else {
     cudaFuncSetAttribute(k_chunk<2, 0>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
-    e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, k_chunk<2, 0>, kThreads, sm);
+    e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, k_chunk<2, 0>, kCThreads, sm);
   }
   if (e != cudaSuccess || n < 1) n = 1;
   return n;
@@ -398,13 +433,13 @@ int launch_copy(const Job& j, u32 grid, cudaStream_t s) {
   return cudaGetLastError() == cudaSuccess ? 1 : -1;
 }
 
-// chunk_max for a record size: the largest range whose staging and index arrays fit the
-// shared memory of two CTAs per SM (and whose positions fit kIdxBits bits).
+// chunk_max for a record size: the largest range whose two staging buffers and index arrays
+// fit the shared memory of the chunk CTA (and whose positions fit kIdxBits bits).
 u32 chunk_capacity(u32 RW) {
   const size_t budget = kChunkSmem - kChunkFixed;
-  u32 m = (u32)(budget / (RW * 8 + 4));  // the record + two u16 index arrays
+  u32 m = (u32)(budget / (2 * RW * 8 + 4));  // two copies of the record + two u16 index arrays
   m &= ~63u;
-  if (m > (u32)kThreads * kChunkItems) m = kThreads * kChunkItems;
+  if (m > (u32)kCThreads * kChunkItems) m = kCThreads * kChunkItems;
   if (m > (1u << kIdxBits)) m = 1u << kIdxBits;
   return m;
 }

@@ -63,7 +63,7 @@ struct Chunk {
   u32 flags;        // kChSrcTmp: records are in tmp (else in); kChCopyOnly: already sorted
   u64 seg_first;    // segmented chunks: first segment (index into the offsets array)
   u32 seg_count;
-  u32 pad;
+  u32 p;            // every key bit >= p is shared by the chunk (0: unknown, compute it)
 };
 
 // A range of finished records that lives in tmp and must be copied to in.
@@ -109,6 +109,8 @@ struct Job {
   u64 cap_base;
   void* status[2];    // look-back words (u32 or u64)
   u64 cap_status;
+  u32* tile_bin;      // bin of every tile of the current level (written by the histogram pass)
+  u64 cap_tiles;
   Chunk* chunks;
   u64 cap_chunks;
   Piece* pieces;
@@ -218,6 +220,24 @@ __device__ __forceinline__ void st_release(u32* p, u32 v) {
 __device__ __forceinline__ void st_release(u64* p, u64 v) {
   asm volatile("st.release.gpu.global.u64 [%0], %1;" ::"l"(p), "l"(v) : "memory");
 }
+// Relaxed (unfenced) device-scope accesses: for words that carry their own payload, such as
+// the look-back words (a state and a count in one word), no ordering with other data is needed.
+__device__ __forceinline__ u32 ld_relaxed(const u32* p) {
+  u32 v;
+  asm volatile("ld.relaxed.gpu.global.u32 %0, [%1];" : "=r"(v) : "l"(p) : "memory");
+  return v;
+}
+__device__ __forceinline__ u64 ld_relaxed(const u64* p) {
+  u64 v;
+  asm volatile("ld.relaxed.gpu.global.u64 %0, [%1];" : "=l"(v) : "l"(p) : "memory");
+  return v;
+}
+__device__ __forceinline__ void st_relaxed(u32* p, u32 v) {
+  asm volatile("st.relaxed.gpu.global.u32 [%0], %1;" ::"l"(p), "r"(v) : "memory");
+}
+__device__ __forceinline__ void st_relaxed(u64* p, u64 v) {
+  asm volatile("st.relaxed.gpu.global.u64 [%0], %1;" ::"l"(p), "l"(v) : "memory");
+}
 
 // Exclusive scan of n u32 values in shared memory, in place, by a CTA of NT threads; returns
 // the total.  All threads of the CTA must call it.  `scratch` holds NT/32 + 1 u32.
@@ -323,6 +343,9 @@ __device__ __forceinline__ void cp_async8(void* smem, const void* gmem) {
   asm volatile("cp.async.ca.shared.global [%0], [%1], 8;\n" ::"r"(s), "l"(gmem) : "memory");
 }
 __device__ __forceinline__ void cp_async_wait_all() { asm volatile("cp.async.wait_all;\n" ::: "memory"); }
+__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;\n" ::: "memory"); }
+// wait until at most one (the most recent) group of this thread's copies is still pending
+__device__ __forceinline__ void cp_async_wait_one() { asm volatile("cp.async.wait_group 1;\n" ::: "memory"); }
 
 // Start copying `words` 8-byte words global -> shared (16-byte copies when the source is
 // 16-byte aligned; the destination always is).  Call cp_async_wait_all + __syncthreads

@@ -225,8 +225,6 @@ __device__ void finish_bin(const Job& j, int L, u64 b, int mode) {
 // is counted).
 __host__ __device__ inline size_t hist_smem_bytes_for(u32 T, u32 KW) { return 2ull * T * KW * 8; }
 
-__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;\n" ::: "memory"); }
-__device__ __forceinline__ void cp_async_wait_one() { asm volatile("cp.async.wait_group 1;\n" ::: "memory"); }
 
 template <int KW>
 __global__ void __launch_bounds__(kThreads, 2) k_hist(Job j, int level, int mode) {
@@ -328,6 +326,7 @@ __global__ void __launch_bounds__(kThreads, 2) k_hist(Job j, int level, int mode
     const u64 tib = t - bp->tile_start;
     const u64 r0 = tib * T;
     tr.cnt = (u32)min((u64)T, bp->size - r0);
+    if ((mode == 0 || mode == 3) && tid == 0 && t < j.cap_tiles) j.tile_bin[t] = (u32)walk;
     if (mode == 0 || mode == 3) {  // the scatter pass's look-back words of this tile start cleared
       const u32 nd = 1u << tr.W;
       const u64 so = bp->status_off + tib * nd;
@@ -394,8 +393,8 @@ __global__ void __launch_bounds__(kThreads, 2) k_hist(Job j, int level, int mode
 constexpr int kSThreads = 256;  // threads of a scatter CTA
 constexpr int kSWarps = kSThreads / 32;
 
-// Shared memory of k_scatter: T records, per-warp digit counters (row stride 2^wmax), the
-// tile's permutation, per-digit counts / run bases / global bases.
+// Shared memory of k_scatter: T records, per-warp 16-bit digit counters (row stride 2^wmax),
+// the tile's permutation, per-digit counts / run bases / global bases.
 struct ScatterLayout {
   size_t stage, whist, perm, tcount, tbase, gbase, total;
 };
@@ -405,7 +404,7 @@ __host__ __device__ inline ScatterLayout scatter_layout(u32 T, u32 RW, u32 wmax)
   const size_t nd = (size_t)1 << wmax;
   size_t o = 0;
   s.stage = o; o += (size_t)T * RW * 8;
-  s.whist = o; o += (size_t)kSWarps * nd * 4;
+  s.whist = o; o += (size_t)kSWarps * nd * 2;
   s.perm = o; o += (size_t)T * 2;
   o = (o + 15) & ~(size_t)15;
   s.tcount = o; o += nd * 4;
@@ -430,21 +429,22 @@ struct LB<u64> {
 };
 
 // Publishes this tile's count of one digit and returns the number of records with that digit
-// in the bin's earlier tiles (decoupled look-back).  Every wait is bounded.
+// in the bin's earlier tiles (decoupled look-back).  A look-back word carries its state and its
+// count together, so plain relaxed accesses suffice (no fences).  Every wait is bounded.
 template <typename S>
 __device__ __forceinline__ u64 look_back(S* st, u64 self, u32 nd, u64 tib, u32 c, const Job& j, bool stall) {
   Ctl* ctl = j.ctl;
   if (tib == 0) {
-    st_release(st + self, (S)(((S)2 << LB<S>::kShift) | (S)c));
+    st_relaxed(st + self, (S)(((S)2 << LB<S>::kShift) | (S)c));
     return 0;
   }
-  st_release(st + self, (S)(((S)1 << LB<S>::kShift) | (S)c));
+  st_relaxed(st + self, (S)(((S)1 << LB<S>::kShift) | (S)c));
   u64 excl = 0;
   u64 idx = self - nd;
   for (u64 back = 1; back <= tib; back++, idx -= nd) {
     // a stalled wait (testing) polls a word that no tile ever writes
     const S* wp = stall && back == 1 ? (const S*)nullptr : st + idx;
-    S w = wp ? ld_acquire(wp) : (S)ld_acquire(&ctl->never);
+    S w = wp ? ld_relaxed(wp) : (S)ld_relaxed(&ctl->never);
     u32 polls = 0;
     while ((w >> LB<S>::kShift) == 0) {
       // give up after `watchdog` polls, or at once when any wait of this call has already
@@ -454,16 +454,18 @@ __device__ __forceinline__ u64 look_back(S* st, u64 self, u32 nd, u64 tib, u32 c
         break;
       }
       __nanosleep(100);
-      w = wp ? ld_acquire(wp) : (S)ld_acquire(&ctl->never);
+      w = wp ? ld_relaxed(wp) : (S)ld_relaxed(&ctl->never);
     }
     excl += (u64)(w & LB<S>::kVal);
     if ((w >> LB<S>::kShift) != 1) break;  // inclusive prefix (or gave up): done
   }
-  st_release(st + self, (S)(((S)2 << LB<S>::kShift) | (S)(excl + c)));
+  st_relaxed(st + self, (S)(((S)2 << LB<S>::kShift) | (S)(excl + c)));
   return excl;
 }
 
-// IT = records per thread (T = kSThreads * IT).
+// IT = records per thread (T = kSThreads * IT).  Tiles are taken one at a time from a ticket
+// dispenser, in order, so that every tile a look-back waits for is already held by a running
+// CTA that will publish its counts without waiting for anything later.
 template <int KW, int RWT, int IT>
 __global__ void __launch_bounds__(kSThreads) k_scatter(Job j, int level) {
   const int L = level & 1;
@@ -479,43 +481,45 @@ __global__ void __launch_bounds__(kSThreads) k_scatter(Job j, int level) {
   const ScatterLayout lay = scatter_layout(T, RW, j.wmax);
   extern __shared__ __align__(16) unsigned char smem[];
   u64* stage = (u64*)(smem + lay.stage);
-  u32* whist = (u32*)(smem + lay.whist);
+  u16* whist = (u16*)(smem + lay.whist);
   u16* perm = (u16*)(smem + lay.perm);
   u32* tcount = (u32*)(smem + lay.tcount);
   u32* tbase = (u32*)(smem + lay.tbase);
   u64* gbase = (u64*)(smem + lay.gbase);
-  __shared__ u64 s_ticket, s_bin;
+  __shared__ u64 s_ticket;
+  __shared__ u32 s_bin;
   __shared__ u32 scan_scr[kSWarps + 1];
   const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
   const u32 ltmask = lanemask_lt();
-  // per-warp counters: low half = this tile's count, high half = the warp's offset within
-  // the digit's run; the prefix pass rewrites each entry as (offset << 16), which also
-  // clears the count for the next tile
+  // per-warp digit counters: counts while ranking, then each warp's offset inside the digit's
+  // run; they are zeroed again while the tile is written out
   for (u32 i = tid; i < kSWarps * WS; i += kSThreads) whist[i] = 0;
-  u32* wh = whist + warp * WS;
+  u16* wh = whist + warp * WS;
 
   for (;;) {
     if (tid == 0) {
       const u64 tk = atomicAdd(&ctl->s_ticket, 1ull);
       s_ticket = tk;
-      s_bin = tk < ntiles ? find_bin(bins, nb, tk) : 0;
+      s_bin = tk < ntiles && tk < j.cap_tiles ? j.tile_bin[tk] : 0;
     }
     __syncthreads();
     const u64 t = s_ticket;
-    const u64 b = s_bin;
+    const u32 b = s_bin;
     __syncthreads();  // every thread has its ticket before thread 0 may take the next
     if (t >= ntiles) break;
-    const Bin bin = bins[b];
-    if (bin.flags & kBinEqual) continue;
-    const u32 lo = bin.lo, W = bin.W, nd = 1u << W;
-    const u64 tib = t - bin.tile_start;
+    const Bin* bp = &bins[b < nb ? b : 0];
+    const u32 lo = bp->lo, W = bp->W, nd = 1u << W;
+    const u64 begin = bp->begin, size = bp->size;
+    const u64 tib = t - bp->tile_start;
+    const u64 status_off = bp->status_off;
+    const u32 parity = bp->parity;
+    if ((bp->flags & kBinEqual) || tib * T >= size) continue;  // finished bin (or inconsistent map)
     const u64 r0 = tib * T;
-    const u32 cnt = (u32)min((u64)T, bin.size - r0);
-    const u64* src = j.buf[bin.parity] + (bin.begin + r0) * RW;
-    u64* dstb = j.buf[bin.parity ^ 1];
-    const u64* bbase = j.base[L] + bin.base_off;
+    const u32 cnt = (u32)min((u64)T, size - r0);
+    u64* dstb = j.buf[parity ^ 1];
+    const u64* bbase = j.base[L] + bp->base_off;
 
-    load_words_async<kSThreads>(stage, src, (u64)cnt * RW);
+    load_words_async<kSThreads>(stage, j.buf[parity] + (begin + r0) * RW, (u64)cnt * RW);
     cp_async_wait_all();
     __syncthreads();
 
@@ -532,9 +536,9 @@ __global__ void __launch_bounds__(kSThreads) k_scatter(Job j, int level) {
       u32 old = 0;
       if (valid) old = wh[d];
       __syncwarp();
-      if (valid && before == 0) wh[d] = old + __popc(peers);
+      if (valid && before == 0) wh[d] = (u16)(old + __popc(peers));
       __syncwarp();
-      packed[it] = valid ? (((old & 0xffffu) + before) | (d << 16)) : 0xffffffffu;
+      packed[it] = valid ? ((old + before) | (d << 16)) : 0xffffffffu;
     }
     __syncthreads();
     for (u32 v = tid; v < nd; v += kSThreads) {
@@ -542,8 +546,8 @@ __global__ void __launch_bounds__(kSThreads) k_scatter(Job j, int level) {
 #pragma unroll
       for (int w = 0; w < kSWarps; w++) {
         const u32 x = whist[w * WS + v];
-        whist[w * WS + v] = run << 16;
-        run += x & 0xffffu;
+        whist[w * WS + v] = (u16)run;
+        run += x;
       }
       tcount[v] = run;
       tbase[v] = run;
@@ -552,24 +556,29 @@ __global__ void __launch_bounds__(kSThreads) k_scatter(Job j, int level) {
     block_exclusive_scan<kSThreads>(tbase, nd, scan_scr);
     // decoupled look-back over the earlier tiles of this bin
     for (u32 v = tid; v < nd; v += kSThreads) {
-      const u64 self = bin.status_off + tib * nd + v;
+      const u64 self = status_off + tib * nd + v;
       const bool stall = j.inject && v == 0 && tib == 1;
       const u64 excl = j.wide ? look_back<u64>((u64*)j.status[L], self, nd, tib, tcount[v], j, stall)
                               : look_back<u32>((u32*)j.status[L], self, nd, tib, tcount[v], j, stall);
-      gbase[v] = bin.begin + bbase[v] + excl - tbase[v];
+      gbase[v] = begin + bbase[v] + excl - tbase[v];
     }
 #pragma unroll
     for (int it = 0; it < IT; it++) {
       if (packed[it] != 0xffffffffu) {
         const u32 d = packed[it] >> 16;
-        perm[tbase[d] + (wh[d] >> 16) + (packed[it] & 0xffffu)] = (u16)(warp * PW + it * 32 + lane);
+        perm[tbase[d] + wh[d] + (packed[it] & 0xffffu)] = (u16)(warp * PW + it * 32 + lane);
       }
     }
     __syncthreads();
+    // per-warp counters back to zero for the next tile (nothing reads them before then)
+    for (u32 v = tid; v < nd; v += kSThreads) {
+#pragma unroll
+      for (int w = 0; w < kSWarps; w++) whist[w * WS + v] = 0;
+    }
     // write the tile in digit order: consecutive slots of one digit go to consecutive
     // records.  A destination outside the bin (possible only after a failed wait or a
     // corrupted histogram, both reported) is skipped, never written.
-    const u64 lo_rec = bin.begin, hi_rec = bin.begin + bin.size;
+    const u64 hi_rec = begin + size;
     bool bad = false;
     if (RW == 2) {
       for (u32 s = tid; s < cnt; s += kSThreads) {
@@ -579,7 +588,7 @@ __global__ void __launch_bounds__(kSThreads) k_scatter(Job j, int level) {
         k.w[0] = v.x & j.keymask[0];
         if (KW == 2) k.w[KW - 1] = v.y & j.keymask[1];
         const u64 dst = gbase[digit_of<KW>(k, lo, W)] + s;
-        if (dst < lo_rec || dst >= hi_rec) { bad = true; continue; }
+        if (dst < begin || dst >= hi_rec) { bad = true; continue; }
         __stcs(reinterpret_cast<ulonglong2*>(dstb + 2 * dst), v);
       }
     } else {
@@ -587,7 +596,7 @@ __global__ void __launch_bounds__(kSThreads) k_scatter(Job j, int level) {
         const u32 r = perm[s];
         const u64* sp = stage + (u64)r * RW;
         const u64 dst = gbase[digit_of<KW>(load_key<KW>(sp, j), lo, W)] + s;
-        if (dst < lo_rec || dst >= hi_rec) { bad = true; continue; }
+        if (dst < begin || dst >= hi_rec) { bad = true; continue; }
         u64* d = dstb + dst * RW;
         for (u32 w = 0; w < RW; w++) __stcs(d + w, sp[w]);
       }
@@ -707,7 +716,7 @@ __global__ void __launch_bounds__(kThreads) k_classify(Job j, int level) {
     if (tid == 0) {
       // greedy packing of consecutive small sub-bins into on-chip chunks
       u64 cb = 0;
-      u32 csz = 0;
+      u32 csz = 0, nsub = 0;
       bool open = false, uns = false;
       auto emit = [&]() {
         if (open && (uns || p1)) {
@@ -719,6 +728,8 @@ __global__ void __launch_bounds__(kThreads) k_classify(Job j, int level) {
             ch.begin = bin.begin + cb;
             ch.size = csz;
             ch.flags = (p1 ? kChSrcTmp : 0u) | (uns ? 0u : kChCopyOnly);
+            // one sub-bin shares every bit >= lo; several also differ in the digit itself
+            ch.p = nsub == 1 ? bin.lo : bin.lo + bin.W;
             j.chunks[idx] = ch;
           }
         }
@@ -733,10 +744,12 @@ __global__ void __launch_bounds__(kThreads) k_classify(Job j, int level) {
           if (!open) {
             cb = boff[v];
             csz = 0;
+            nsub = 0;
             uns = false;
             open = true;
           }
           csz += sz;
+          nsub++;
           if (k == 2) uns = true;
         } else {
           emit();
@@ -808,7 +821,8 @@ static cudaError_t scatter_it(const Job& j, int level, u32 grid, cudaStream_t s,
     case 16: return scatter_rw<KW, 16>(j, level, grid, s, occ);
     case 8: return scatter_rw<KW, 8>(j, level, grid, s, occ);
     case 4: return scatter_rw<KW, 4>(j, level, grid, s, occ);
-    default: return scatter_rw<KW, 2>(j, level, grid, s, occ);
+    case 2: return scatter_rw<KW, 2>(j, level, grid, s, occ);
+    default: return scatter_rw<KW, 1>(j, level, grid, s, occ);
   }
 }
 

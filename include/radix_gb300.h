@@ -165,6 +165,43 @@ rs_status radix_sort_profile(int enable);
 int64_t radix_sort_profile_read(rs_kernel_time *out, int64_t max);
 
 /*
+ * radix_sort without any allocation.  (No counterpart in the paper: this is an interface
+ * for callers that cannot allocate.)
+ *
+ * Some callers must not have a library allocate device memory behind their back: a
+ * framework whose caching allocator owns the GPU's memory (an outside cudaMalloc can fail
+ * or fragment it), a latency-critical path where cudaMalloc/cudaFree would add an implicit
+ * device synchronisation, or a process with a fixed device-memory budget.  radix_sort
+ * allocates its metadata workspace on first use; this entry point instead uses a fixed
+ * array of 64 MiB in device memory that the library declares statically (every GPU that
+ * loads the library holds it until the process exits).  It calls no cudaMalloc, cudaFree or
+ * other allocating routine.
+ *
+ * Arguments and result are those of radix_sort; the sort is the same (byte-identical
+ * output).  Additionally:
+ *   d_status  optional DEVICE pointer to one uint32: when the call's work has run it holds
+ *             the call's device-side status (0 = ok; nonzero = a bounded wait gave up or a
+ *             range check failed, as radix_sort_status reports for radix_sort).  NULL: none.
+ *             (radix_sort_status does not see calls made through this entry point.)
+ * Limits:
+ *   The workspace needed for (n, rec_size, key_size) must fit the 64 MiB array, else the
+ *   call returns RS_ERR_TOO_LARGE and launches nothing.  With the default plan that is about
+ *   4.0 x 10^7 records of 16 bytes (8-byte keys), 5.1 x 10^7 of 8 bytes, 2.5 x 10^7 of
+ *   24 bytes (16-byte keys).
+ * Sharing:
+ *   Every call uses the same array, on every stream.  Calls whose work overlaps on the GPU
+ *   (on different streams, or from different host threads without ordering) race on it and
+ *   produce undefined results: order them on one stream or synchronise between them.
+ *   The array keeps the previous call's contents; each call resets what it relies on.
+ * Set-up:
+ *   The first call on a device looks up the array's device address on that device (the
+ *   address is then kept).  Make that first call on each device before capturing a stream
+ *   into a CUDA graph.
+ */
+rs_status radix_sort_noalloc(void *in, void *tmp, uint64_t n, uint32_t rec_size, uint32_t key_size,
+                             uint32_t *d_status, rs_stream_t stream);
+
+/*
  * Testing only.  flags = 1: in the next call, the first look-back wait of each distribution
  * pass waits on a device word that nothing writes, so the bounded wait must give up:
  * the call completes, its result is undefined, and radix_sort_status() reports

@@ -275,6 +275,115 @@ static rs_status run_levels(const Setup& st, cudaStream_t s) {
   return RS_OK;
 }
 
+// ------------------------------------------------------------- no-allocation variant
+// Workspace of radix_sort_noalloc: a fixed array in device memory that every GPU which loads
+// this library holds until the process exits.  Its size bounds the sorts that entry point
+// accepts (see noalloc_setup).
+constexpr size_t kNoAllocBytes = 64ull << 20;
+static __device__ __align__(256) unsigned char g_noalloc_ws[kNoAllocBytes];
+
+constexpr int kNoAllocMaxDevices = 64;
+static std::mutex g_na_mu;
+static void* g_na_ptr[kNoAllocMaxDevices];  // device address of g_noalloc_ws, per device
+
+// The array's address on the current device.  In host code g_noalloc_ws names a host-side
+// stand-in, not device memory, so the address is looked up once per device (with that device
+// current) and kept.
+static rs_status noalloc_address(int dev, void** out) {
+  if (dev < 0 || dev >= kNoAllocMaxDevices) return RS_ERR_CUDA;
+  std::lock_guard<std::mutex> lk(g_na_mu);
+  if (!g_na_ptr[dev]) {
+    void* p = nullptr;
+    const cudaError_t e = cudaGetSymbolAddress(&p, g_noalloc_ws);
+    if (e != cudaSuccess || !p) {
+      cudaGetLastError();
+      return RS_ERR_CUDA;
+    }
+    g_na_ptr[dev] = p;
+  }
+  *out = g_na_ptr[dev];
+  return RS_OK;
+}
+
+// The job of radix_sort_noalloc: the same plan as radix_sort, its workspace carved from the
+// fixed array.  RS_ERR_TOO_LARGE when that workspace would not fit.
+static rs_status noalloc_setup(void* in, void* tmp, u64 n, u32 rec_size, u32 key_size, Setup* st) {
+  Job& j = st->j;
+  memset(&j, 0, sizeof j);
+  j.buf[0] = (u64*)in;
+  j.buf[1] = (u64*)tmp;
+  j.n = n;
+  j.RW = rec_size / 8;
+  j.K = key_size;
+  j.KW = key_size > 8 ? 2 : 1;
+  for (u32 w = 0; w < 2; w++) {
+    const int bytes = (int)key_size - 8 * (int)w;
+    j.keymask[w] = bytes >= 8 ? ~0ull : bytes <= 0 ? 0ull : ((1ull << (8 * bytes)) - 1);
+  }
+  rs_plan p;
+  {
+    std::lock_guard<std::mutex> lk(g_mu);
+    p = g_plan;
+  }
+  j.wmax = p.digit_bits_max ? p.digit_bits_max : 9;
+  u32 T = 4096;
+  while (T > 256 && (u64)T * rec_size > 65536) T >>= 1;
+  if (p.tile_records) T = p.tile_records;
+  j.T = T;
+  const u32 cap = chunk_capacity(j.RW);
+  j.chunk_max = p.chunk_records && p.chunk_records < cap ? p.chunk_records : cap;
+  j.watchdog = p.watchdog_polls ? p.watchdog_polls : (1u << 16);
+  j.wide = n >= (1ull << 30) ? 1u : 0u;
+  const Caps c = caps_for(n, j.T, j.chunk_max, j.wmax, j.wide != 0, 0);
+  if (c.bytes > kNoAllocBytes) return RS_ERR_TOO_LARGE;
+  st->c = c;
+  return RS_OK;
+}
+
+static void noalloc_carve(Setup* st, char* base) {
+  Job& j = st->j;
+  const Caps& c = st->c;
+  j.ctl = (Ctl*)(base + c.off_ctl);
+  j.bins[0] = (Bin*)(base + c.off_bins0);
+  j.bins[1] = (Bin*)(base + c.off_bins1);
+  j.cap_bins = c.bins;
+  j.base[0] = (u64*)(base + c.off_base0);
+  j.base[1] = (u64*)(base + c.off_base1);
+  j.cap_base = c.base;
+  j.status[0] = j.status[1] = base + c.off_status;
+  j.cap_status = c.status;
+  j.chunks = (Chunk*)(base + c.off_chunks);
+  j.cap_chunks = c.chunks;
+  j.pieces = (Piece*)(base + c.off_pieces);
+  j.cap_pieces = c.pieces;
+  j.tile_bin = (u32*)(base + c.off_tiles);
+  j.cap_tiles = c.tiles;
+}
+
+// The level sequence of run_levels, launched without the optional timing events.
+static rs_status noalloc_levels(const Setup& st, cudaStream_t s) {
+  const Job& j = st.j;
+  const u32 gh = (u32)st.sms * (u32)hist_ctas_per_sm(j);
+  const u32 gs = (u32)st.sms * (u32)scatter_ctas_per_sm(j, j.wide != 0);
+  const u32 gc = (u32)st.sms * 2;
+  int k;
+  for (int lv = 0; lv < (int)j.K; lv++) {
+    if ((k = launch_hist(j, lv, 0, gh, s)) < 0) return RS_ERR_CUDA;
+    count(k);
+    if ((k = launch_hist(j, lv, 1, gh, s)) < 0) return RS_ERR_CUDA;
+    count(k);
+    if ((k = launch_scatter(j, lv, j.wide != 0, gs, s)) < 0) return RS_ERR_CUDA;
+    count(k);
+    if ((k = launch_classify(j, lv, gc, s)) < 0) return RS_ERR_CUDA;
+    count(k);
+  }
+  if ((k = launch_chunks(j, (u32)st.sms * (u32)chunk_ctas_per_sm(j), s)) < 0) return RS_ERR_CUDA;
+  count(k);
+  if ((k = launch_copy(j, (u32)st.sms * 2, s)) < 0) return RS_ERR_CUDA;
+  count(k);
+  return RS_OK;
+}
+
 }  // namespace rsg
 
 using namespace rsg;
@@ -482,6 +591,58 @@ int64_t radix_sort_profile_read(rs_kernel_time* out, int64_t max) {
     k++;
   }
   return out ? k : (int64_t)g_prof.size();
+}
+
+rs_status radix_sort_noalloc(void* in, void* tmp, uint64_t n, uint32_t rec_size, uint32_t key_size,
+                             uint32_t* d_status, rs_stream_t stream) {
+  rs_status r = validate_layout(rec_size, key_size);
+  if (r != RS_OK) return r;
+  if (n > UINT64_MAX / rec_size) return RS_ERR_TOO_LARGE;
+  Setup st;
+  if ((r = noalloc_setup(in, tmp, n, rec_size, key_size, &st)) != RS_OK) return r;  // size check first
+  cudaStream_t s = (cudaStream_t)stream;
+  if (n <= 1) {
+    if (d_status && cudaMemsetAsync(d_status, 0, sizeof(uint32_t), s) != cudaSuccess) return RS_ERR_CUDA;
+    return RS_OK;
+  }
+  if ((r = validate_buffers(in, tmp, n, rec_size)) != RS_OK) return r;
+  if (check_device_ptr(in) != RS_OK || check_device_ptr(tmp) != RS_OK) return RS_ERR_INVALID_ARG;
+  if (d_status && check_device_ptr(d_status) != RS_OK) return RS_ERR_INVALID_ARG;
+  int dev = 0;
+  if (cudaGetDevice(&dev) != cudaSuccess) return RS_ERR_CUDA;
+  void* ws = nullptr;
+  if ((r = noalloc_address(dev, &ws)) != RS_OK) return r;
+  noalloc_carve(&st, (char*)ws);
+  int sms = 0;
+  if (cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess || sms <= 0) return RS_ERR_CUDA;
+  rs_plan p;
+  {
+    std::lock_guard<std::mutex> lk(g_mu);
+    p = g_plan;
+  }
+  if (p.sm_limit && (int)p.sm_limit < sms) sms = (int)p.sm_limit;
+  st.sms = sms;
+  st.dev = dev;
+  const Job& j = st.j;
+  // the array keeps the previous call's contents: its error word starts this call at zero,
+  // and the init kernels rewrite the rest of the control block and the first bin list
+  if (cudaMemsetAsync(&j.ctl->err, 0, sizeof(u32), s) != cudaSuccess) return RS_ERR_CUDA;
+  int k;
+  if (n <= j.chunk_max) {
+    if ((k = launch_init_single_chunk(j, s)) < 0) return RS_ERR_CUDA;
+    count(k);
+    if ((k = launch_chunks(j, 1, s)) < 0) return RS_ERR_CUDA;
+    count(k);
+  } else {
+    u32 lo, W;
+    plan_digit(n, 8 * key_size, j.chunk_max, j.wmax, &lo, &W);
+    if ((k = launch_init_plain(j, lo, W, s)) < 0) return RS_ERR_CUDA;
+    count(k);
+    if ((r = noalloc_levels(st, s)) != RS_OK) return r;
+  }
+  if (d_status && cudaMemcpyAsync(d_status, &j.ctl->err, sizeof(uint32_t), cudaMemcpyDeviceToDevice, s) != cudaSuccess)
+    return RS_ERR_CUDA;
+  return RS_OK;
 }
 
 rs_status radix_sort_test_inject(uint32_t flags) {

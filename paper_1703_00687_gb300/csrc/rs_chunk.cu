@@ -110,18 +110,43 @@ __device__ void scan_counts(const ChunkCtx<KW, RWT>& c, u32 nd) {
   __syncthreads();
 }
 
+// The digit of an on-chip distribution: key bits [lo, lo + w), optionally preceded (as more
+// significant bits) by a packed chunk's sub-bin number, (parent digit - v0) on sb bits.
+struct DigitSpec {
+  u32 lo, w;        // window below the shared bits
+  u32 plo, pw, v0;  // the parent digit of a packed chunk: key bits [plo, plo + pw)
+  u32 sb;           // bits of the sub-bin number (0: not packed)
+  __device__ __forceinline__ u32 bits() const { return sb + w; }
+  template <int KW>
+  __device__ __forceinline__ u32 of(const Key<KW>& k) const {
+    u32 d = digit_of<KW>(k, lo, w);
+    if (sb) d |= (digit_of<KW>(k, plo, pw) - v0) << w;
+    return d;
+  }
+};
+
+// Window of kWinBits bits right below bit p (all bits >= p shared), no sub-bin number.
+__device__ __forceinline__ DigitSpec window_below(u32 p) {
+  DigitSpec d = {};
+  d.w = p > (u32)kWinBits ? (u32)kWinBits : p;
+  d.lo = p - d.w;
+  return d;
+}
+
 // Distributes positions [a, a + s) of c.perm into c.out by a digit of the record (any order
 // inside a bucket); afterwards c.cnt holds every bucket's first position (relative to a).
-// by_index: the digit is the record's input position (unique); else key bits [lo, lo + w).
-// identity: c.perm is the identity over the range (not read).
+// by_index: the digit is the record's input position (unique); else dig.
+// identity: c.perm is the identity over the range (not read).  zeroed: c.cnt is already 0.
 template <int KW, int RWT>
-__device__ void distribute(const ChunkCtx<KW, RWT>& c, u32 a, u32 s, bool by_index, u32 lo, u32 w,
-                           bool identity = false) {
+__device__ void distribute(const ChunkCtx<KW, RWT>& c, u32 a, u32 s, bool by_index, const DigitSpec& dig,
+                           bool identity, bool zeroed) {
   const int tid = threadIdx.x;
-  const u32 nd = by_index ? (1u << kIdxBits) : (1u << w);
+  const u32 nd = by_index ? (1u << kIdxBits) : (1u << dig.bits());
   const u32 words = (nd + 1) >> 1;
-  for (u32 i = tid; i < words; i += kCThreads) c.cnt[i] = 0;
-  __syncthreads();
+  if (!zeroed) {
+    for (u32 i = tid; i < words; i += kCThreads) c.cnt[i] = 0;
+    __syncthreads();
+  }
   u32 held[kChunkItems];
 #pragma unroll
   for (int k = 0; k < kChunkItems; k++) {
@@ -129,7 +154,7 @@ __device__ void distribute(const ChunkCtx<KW, RWT>& c, u32 a, u32 s, bool by_ind
     held[k] = 0xffffffffu;
     if (i < s) {
       const u32 r = identity ? a + i : c.perm[a + i];
-      const u32 d = by_index ? r : digit_of<KW>(c.key(r), lo, w);
+      const u32 d = by_index ? r : dig.of<KW>(c.key(r));
       const u32 old = atomicAdd(&c.cnt[d >> 1], 1u << ((d & 1) * 16));
       held[k] = (((old >> ((d & 1) * 16)) & 0xffffu)) | (d << 16);
     }
@@ -147,19 +172,19 @@ __device__ void distribute(const ChunkCtx<KW, RWT>& c, u32 a, u32 s, bool by_ind
   __syncthreads();
 }
 
-// Sorts positions [a, a + s) of c.perm by (key, input position), given that every key bit >= p
-// is shared by the range.  Buckets longer than kEsMax go on the stack.
+// Sorts positions [a, a + s) of c.perm by (key, input position): one distribution by `dig`,
+// then enumeration sort of every bucket of up to kEsMax records; larger buckets go on the
+// stack.  Ends with a barrier, after which *s_top is final.
 template <int KW, int RWT>
-__device__ void sort_round(const ChunkCtx<KW, RWT>& c, u32 a, u32 s, u32 p, u32* s_top, bool identity = false) {
+__device__ void sort_round(const ChunkCtx<KW, RWT>& c, u32 a, u32 s, const DigitSpec& dig, u32* s_top,
+                           bool identity = false, bool zeroed = false) {
   const int tid = threadIdx.x;
-  const u32 w = p > (u32)kWinBits ? (u32)kWinBits : p;
-  const u32 lo = p - w;
-  const u32 nd = 1u << w;
-  distribute(c, a, s, false, lo, w, identity);
+  const u32 nd = 1u << dig.bits();
+  distribute(c, a, s, false, dig, identity, zeroed);
   for (u32 i = tid; i < s; i += kCThreads) {
     const u32 r = c.out[a + i];
     const Key<KW> kr = c.key(r);
-    const u32 d = digit_of<KW>(kr, lo, w);
+    const u32 d = dig.of<KW>(kr);
     const u32 st = c.count_of(d);
     const u32 en = d + 1 < nd ? c.count_of(d + 1) : s;
     const u32 sz = en - st;
@@ -279,6 +304,7 @@ __global__ void __launch_bounds__(kCThreads, 1) k_chunk(Job j) {
     cp_async_commit();
   };
 
+  for (u32 i = tid; i < (u32)kCntWords; i += kCThreads) c.cnt[i] = 0;
   if (tid == 0) {
     fetch(0, atomicAdd(&ctl->chunk_ticket, 1ull));
     fetch(1, atomicAdd(&ctl->chunk_ticket, 1ull));
@@ -293,21 +319,39 @@ __global__ void __launch_bounds__(kCThreads, 1) k_chunk(Job j) {
     if (s_t[cur] >= nch) break;  // tickets are taken in order: no later chunk either
     const Chunk ch = s_ch[cur];
     u64 nt = 0;
-    if (tid == 0) nt = atomicAdd(&ctl->chunk_ticket, 1ull);  // used at the end of this chunk
+    if (tid == 0) nt = atomicAdd(&ctl->chunk_ticket, 1ull);  // described during this chunk
     const u32 sz = ch.size;
     c.stage = stage0 + (size_t)cur * m * RW;
     const u64* stage = c.stage;
     u64* dst = j.buf[0] + ch.begin * RW;
     const bool in_place = !(ch.flags & kChSrcTmp);
-    u32 p = 0;
-    if (sz && !(ch.flags & kChCopyOnly)) p = ch.p ? ch.p : range_top_bit(c, 0, sz, false);
-    if (sz && p) {
+    DigitSpec dig = {};
+    bool sort = sz && !(ch.flags & kChCopyOnly);
+    if (sort) {
+      if (ch.p) {  // shared bits known from the level that produced the chunk
+        dig = window_below(ch.p);
+        if (ch.sb) {
+          dig.sb = ch.sb;
+          dig.plo = ch.p;
+          dig.pw = ch.pw;
+          dig.v0 = ch.v0;
+          dig.w = ch.p > (u32)kWinBits - ch.sb ? (u32)kWinBits - ch.sb : ch.p;
+          dig.lo = ch.p - dig.w;
+        }
+      } else {
+        const u32 p = range_top_bit(c, 0, sz, false);  // (ends with a barrier)
+        sort = p != 0;
+        dig = window_below(p);
+      }
+    }
+    if (sort) {
       if (tid == 0) s_top = 0;
-      sort_round(c, 0, sz, p, &s_top, true);
-      for (;;) {
-        __syncthreads();
+      // s_ch[cur] has been read by every thread (a barrier lies inside sort_round before
+      // thread 0 rewrites it below)
+      sort_round(c, 0, sz, dig, &s_top, true, true);
+      if (tid == 0) fetch(cur, nt);
+      while (s_top) {  // s_top is final after the barrier that ends every round
         const u32 top = s_top;
-        if (top == 0) break;
         if (top > c.stack_cap) {  // cannot happen: buckets on the stack are disjoint and > kEsMax
           if (tid == 0) atomicOr(&ctl->err, kErrInternal);
           break;
@@ -318,13 +362,15 @@ __global__ void __launch_bounds__(kCThreads, 1) k_chunk(Job j) {
         __syncthreads();
         const u32 pp = range_top_bit(c, a, s, true);
         if (pp) {
-          sort_round(c, a, s, pp, &s_top);
+          sort_round(c, a, s, window_below(pp), &s_top);
         } else {  // all keys equal: back to input order
-          distribute(c, a, s, true, 0, 0);
+          distribute(c, a, s, true, DigitSpec{}, false, false);
           for (u32 i = tid; i < s; i += kCThreads) c.perm[a + i] = c.out[a + i];
+          __syncthreads();
         }
       }
-      __syncthreads();
+      // counters back to zero for the next chunk's first distribution
+      for (u32 i = tid; i < (u32)kCntWords; i += kCThreads) c.cnt[i] = 0;
       // write the records in sorted order
       if (RW == 2) {
         for (u32 s = tid; s < sz; s += kCThreads) {
@@ -343,13 +389,15 @@ __global__ void __launch_bounds__(kCThreads, 1) k_chunk(Job j) {
           for (u32 w = 0; w < RW; w++) __stcs(dst + (u64)s * RW + w, sp[w]);
         }
       }
-    } else if (sz && !in_place) {  // already in order, but in tmp
-      const u64 words = (u64)sz * RW;
-      for (u64 i = tid; i < words; i += kCThreads) __stcs(dst + i, stage[i]);
+    } else {
+      if (sz && !in_place) {  // already in order, but in tmp
+        const u64 words = (u64)sz * RW;
+        for (u64 i = tid; i < words; i += kCThreads) __stcs(dst + i, stage[i]);
+      }
+      __syncthreads();  // every thread has read s_ch[cur]
+      if (tid == 0) fetch(cur, nt);
     }
-    __syncthreads();  // stage buffer `cur` is free
-    if (tid == 0) fetch(cur, nt);
-    __syncthreads();
+    __syncthreads();  // stage buffer `cur` is free and s_ch[cur] describes the next chunk
     issue(cur);
     cur ^= 1;
   }

@@ -64,6 +64,11 @@ struct Chunk {
   u64 seg_first;    // segmented chunks: first segment (index into the offsets array)
   u32 seg_count;
   u32 p;            // every key bit >= p is shared by the chunk (0: unknown, compute it)
+  // A chunk packed from several sub-bins of one parent: they differ in the parent's digit
+  // (key bits [p, p + pw)), whose values lie in [v0, v0 + 2^sb).  The chunk's first
+  // distribution then uses (digit - v0) above the bits right below p.  sb = 0: one sub-bin.
+  u32 v0;
+  u16 pw, sb;
 };
 
 // A range of finished records that lives in tmp and must be copied to in.

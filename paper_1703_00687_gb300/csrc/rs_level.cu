@@ -396,7 +396,7 @@ constexpr int kSWarps = kSThreads / 32;
 // Shared memory of k_scatter: T records, per-warp 16-bit digit counters (row stride 2^wmax),
 // the tile's permutation, per-digit counts / run bases / global bases.
 struct ScatterLayout {
-  size_t stage, whist, perm, tcount, tbase, gbase, total;
+  size_t stage, whist, perm, sdig, tcount, tbase, gbase, total;
 };
 
 __host__ __device__ inline ScatterLayout scatter_layout(u32 T, u32 RW, u32 wmax) {
@@ -406,6 +406,7 @@ __host__ __device__ inline ScatterLayout scatter_layout(u32 T, u32 RW, u32 wmax)
   s.stage = o; o += (size_t)T * RW * 8;
   s.whist = o; o += (size_t)kSWarps * nd * 2;
   s.perm = o; o += (size_t)T * 2;
+  s.sdig = o; o += (size_t)T * 2;
   o = (o + 15) & ~(size_t)15;
   s.tcount = o; o += nd * 4;
   s.tbase = o; o += nd * 4;
@@ -430,37 +431,121 @@ struct LB<u64> {
 
 // Publishes this tile's count of one digit and returns the number of records with that digit
 // in the bin's earlier tiles (decoupled look-back).  A look-back word carries its state and its
-// count together, so plain relaxed accesses suffice (no fences).  Every wait is bounded.
+// count together, so plain relaxed accesses suffice (no fences).  The words of up to
+// LookAhead<S>::n earlier tiles are read together, one round trip per group.  Every wait is bounded.
 template <typename S>
-__device__ __forceinline__ u64 look_back(S* st, u64 self, u32 nd, u64 tib, u32 c, const Job& j, bool stall) {
+struct LookAhead {  // predecessors read per round trip (fewer for the rare 64-bit words: registers)
+  static constexpr int n = sizeof(S) == 4 ? 8 : 3;
+};
+
+template <typename S>
+__device__ __forceinline__ void lb_publish(S* st, u64 self, u64 tib, u32 c) {
+  st_relaxed(st + self, (S)(((S)(tib == 0 ? 2 : 1) << LB<S>::kShift) | (S)c));
+}
+
+template <typename S>
+__device__ __forceinline__ S lb_word(const S* st, u64 at, bool stall, Ctl* ctl) {
+  return stall ? (S)ld_relaxed(&ctl->never) : ld_relaxed(st + at);
+}
+
+// Reads the words of the LookAhead<S>::n tiles before this one (one round trip).
+template <typename S>
+__device__ __forceinline__ void lb_first(const S* st, u64 self, u32 nd, u64 tib, bool stall, Ctl* ctl, S (&w)[LookAhead<S>::n]) {
+#pragma unroll
+  for (int q = 0; q < LookAhead<S>::n; q++)
+    if ((u64)q < tib) w[q] = lb_word(st, self - (u64)(q + 1) * nd, stall && q == 0, ctl);
+}
+
+// Walks back from the words lb_first read, waiting (bounded) for tiles not yet published and
+// reading further groups while only aggregates are found; then publishes the inclusive prefix.
+template <typename S>
+__device__ __forceinline__ u64 lb_collect(S* st, u64 self, u32 nd, u64 tib, u32 c, const Job& j, bool stall, S (&w)[LookAhead<S>::n]) {
   Ctl* ctl = j.ctl;
-  if (tib == 0) {
-    st_relaxed(st + self, (S)(((S)2 << LB<S>::kShift) | (S)c));
-    return 0;
-  }
-  st_relaxed(st + self, (S)(((S)1 << LB<S>::kShift) | (S)c));
+  if (tib == 0) return 0;
   u64 excl = 0;
-  u64 idx = self - nd;
-  for (u64 back = 1; back <= tib; back++, idx -= nd) {
-    // a stalled wait (testing) polls a word that no tile ever writes
-    const S* wp = stall && back == 1 ? (const S*)nullptr : st + idx;
-    S w = wp ? ld_relaxed(wp) : (S)ld_relaxed(&ctl->never);
-    u32 polls = 0;
-    while ((w >> LB<S>::kShift) == 0) {
-      // give up after `watchdog` polls, or at once when any wait of this call has already
-      // given up (the result is then undefined and reported)
-      if (++polls > j.watchdog || ((polls & 255) == 0 && (*(volatile u32*)&ctl->err & kErrTimeout))) {
-        atomicOr(&ctl->err, kErrTimeout);
-        break;
+  u64 back = 1;  // distance of w[0]
+  bool done = false;
+  for (;;) {
+    const u64 n = min((u64)LookAhead<S>::n, tib - back + 1);
+#pragma unroll
+    for (int q = 0; q < LookAhead<S>::n && !done; q++) {
+      if ((u64)q >= n) break;
+      u32 polls = 0;
+      while ((w[q] >> LB<S>::kShift) == 0) {  // a tile not yet published
+        if (++polls > j.watchdog || ((polls & 255) == 0 && (*(volatile u32*)&ctl->err & kErrTimeout))) {
+          atomicOr(&ctl->err, kErrTimeout);
+          break;
+        }
+        __nanosleep(100);
+        w[q] = lb_word(st, self - (back + q) * nd, stall && back + q == 1, ctl);
       }
-      __nanosleep(100);
-      w = wp ? ld_relaxed(wp) : (S)ld_relaxed(&ctl->never);
+      excl += (u64)(w[q] & LB<S>::kVal);
+      if ((w[q] >> LB<S>::kShift) != 1) done = true;  // inclusive prefix (or gave up)
     }
-    excl += (u64)(w & LB<S>::kVal);
-    if ((w >> LB<S>::kShift) != 1) break;  // inclusive prefix (or gave up): done
+    back += n;
+    if (done || back > tib) break;
+#pragma unroll
+    for (int q = 0; q < LookAhead<S>::n; q++)
+      if ((u64)q < tib - back + 1) w[q] = ld_relaxed(st + self - (back + q) * nd);
   }
   st_relaxed(st + self, (S)(((S)2 << LB<S>::kShift) | (S)(excl + c)));
   return excl;
+}
+
+// Lanes of the warp whose digit equals this lane's (d has W significant bits): one vote per
+// digit bit.  Lanes with valid == false get a mask of their own.
+__device__ __forceinline__ u32 peers_of(u32 d, u32 W, bool valid) {
+  u32 peers = __ballot_sync(kFull, valid);
+  for (u32 b = 0; b < W; b++) {
+    const bool bit = (d >> b) & 1u;
+    const u32 v = __ballot_sync(kFull, bit);
+    peers &= bit ? v : ~v;
+  }
+  return valid ? peers : (1u << (threadIdx.x & 31));
+}
+
+// Digit of a staged record.  No key mask is needed: a digit window never reaches past the key.
+template <int KW>
+__device__ __forceinline__ u32 staged_digit(const u64* rec, u32 lo, u32 W) {
+  Key<KW> k;
+  k.w[0] = rec[0];
+  if (KW == 2) k.w[KW - 1] = rec[1];
+  return digit_of<KW>(k, lo, W);
+}
+
+constexpr u64 kSkip = ~0ull;  // gbase of a digit whose run would leave its bin
+
+// Turns the tile's digit counts into destinations: the exclusive scan over digits (tbase) and,
+// per digit, the records of that digit in the bin's earlier tiles (decoupled look-back).  The
+// first look-back words are read before the scan so that the scan hides their round trip.  A
+// digit run that would leave the bin (possible only after a failed wait or a corrupted
+// histogram) gets kSkip and is not written.
+template <typename S, u32 Q>
+__device__ __forceinline__ void tile_offsets(S* st, u64 status_off, u64 tib, u32 nd, const u32* tcount, u32* tbase,
+                                             u32* scan_scr, const u64 (&mybase)[Q], u64 begin, u64 size, const Job& j,
+                                             u64* gbase) {
+  const u32 tid = threadIdx.x;
+  block_exclusive_scan<kSThreads>(tbase, nd, scan_scr);
+  S w[Q][LookAhead<S>::n];
+#pragma unroll
+  for (u32 q = 0; q < Q; q++) {
+    const u32 v = tid + q * kSThreads;
+    if (v < nd) lb_first<S>(st, status_off + tib * nd + v, nd, tib, j.inject && v == 0 && tib == 1, j.ctl, w[q]);
+  }
+#pragma unroll
+  for (u32 q = 0; q < Q; q++) {
+    const u32 v = tid + q * kSThreads;
+    if (v >= nd) break;
+    const u32 c = tcount[v];
+    const u64 excl = lb_collect<S>(st, status_off + tib * nd + v, nd, tib, c, j, j.inject && v == 0 && tib == 1, w[q]);
+    const u64 first = mybase[q] + excl;  // the run's first record, relative to the bin
+    u64 g = begin + first - tbase[v];
+    if (c && (first > size || c > size - first)) {
+      atomicOr(&j.ctl->err, kErrInternal);
+      g = kSkip;
+    }
+    gbase[v] = g;
+  }
 }
 
 // IT = records per thread (T = kSThreads * IT).  Tiles are taken one at a time from a ticket
@@ -477,12 +562,14 @@ __global__ void __launch_bounds__(kSThreads) k_scatter(Job j, int level) {
   const u32 RW = RWT ? (u32)RWT : j.RW;
   constexpr u32 T = kSThreads * IT;
   constexpr u32 PW = T / kSWarps;  // records per warp strip
+  constexpr u32 kDigitsPerThread = (1u << kWMax) / kSThreads;
   const u32 WS = 1u << j.wmax;     // row stride of the per-warp counters
   const ScatterLayout lay = scatter_layout(T, RW, j.wmax);
   extern __shared__ __align__(16) unsigned char smem[];
   u64* stage = (u64*)(smem + lay.stage);
   u16* whist = (u16*)(smem + lay.whist);
   u16* perm = (u16*)(smem + lay.perm);
+  u16* sdig = (u16*)(smem + lay.sdig);
   u32* tcount = (u32*)(smem + lay.tcount);
   u32* tbase = (u32*)(smem + lay.tbase);
   u64* gbase = (u64*)(smem + lay.gbase);
@@ -495,7 +582,6 @@ __global__ void __launch_bounds__(kSThreads) k_scatter(Job j, int level) {
   // run; they are zeroed again while the tile is written out
   for (u32 i = tid; i < kSWarps * WS; i += kSThreads) whist[i] = 0;
   u16* wh = whist + warp * WS;
-
   for (;;) {
     if (tid == 0) {
       const u64 tk = atomicAdd(&ctl->s_ticket, 1ull);
@@ -520,25 +606,51 @@ __global__ void __launch_bounds__(kSThreads) k_scatter(Job j, int level) {
     const u64* bbase = j.base[L] + bp->base_off;
 
     load_words_async<kSThreads>(stage, j.buf[parity] + (begin + r0) * RW, (u64)cnt * RW);
+    u64 mybase[kDigitsPerThread];  // this thread's digits' bucket bases, fetched during the load
+#pragma unroll
+    for (u32 q = 0; q < kDigitsPerThread; q++) {
+      const u32 v = tid + q * kSThreads;
+      mybase[q] = v < nd ? bbase[v] : 0;
+    }
     cp_async_wait_all();
     __syncthreads();
 
     // stable rank: warp w owns records [w*PW, (w+1)*PW), visited in order
     u32 packed[IT];
+    if (cnt == T) {
+      // first every item's digit and peers (independent of each other), then the counters
+      u32 dg[IT], pr[IT];
 #pragma unroll
-    for (int it = 0; it < IT; it++) {
-      const u32 r = warp * PW + it * 32 + lane;
-      const bool valid = r < cnt;
-      u32 d = 0;
-      if (valid) d = digit_of<KW>(load_key<KW>(stage + (u64)r * RW, j), lo, W);
-      const u32 peers = __match_any_sync(kFull, valid ? d : (0x10000u | lane));
-      const u32 before = __popc(peers & ltmask);
-      u32 old = 0;
-      if (valid) old = wh[d];
-      __syncwarp();
-      if (valid && before == 0) wh[d] = (u16)(old + __popc(peers));
-      __syncwarp();
-      packed[it] = valid ? ((old + before) | (d << 16)) : 0xffffffffu;
+      for (int it = 0; it < IT; it++) {
+        dg[it] = staged_digit<KW>(stage + (u64)(warp * PW + it * 32 + lane) * RW, lo, W);
+        pr[it] = peers_of(dg[it], W, true);
+      }
+#pragma unroll
+      for (int it = 0; it < IT; it++) {
+        const u32 d = dg[it], peers = pr[it];
+        const u32 before = __popc(peers & ltmask);
+        const u32 old = wh[d];
+        __syncwarp();
+        if (before == 0) wh[d] = (u16)(old + __popc(peers));
+        __syncwarp();
+        packed[it] = (old + before) | (d << 16);
+      }
+    } else {
+#pragma unroll
+      for (int it = 0; it < IT; it++) {
+        const u32 r = warp * PW + it * 32 + lane;
+        const bool valid = r < cnt;
+        u32 d = 0;
+        if (valid) d = staged_digit<KW>(stage + (u64)r * RW, lo, W);
+        const u32 peers = peers_of(d, W, valid);
+        const u32 before = __popc(peers & ltmask);
+        u32 old = 0;
+        if (valid) old = wh[d];
+        __syncwarp();
+        if (valid && before == 0) wh[d] = (u16)(old + __popc(peers));
+        __syncwarp();
+        packed[it] = valid ? ((old + before) | (d << 16)) : 0xffffffffu;
+      }
     }
     __syncthreads();
     for (u32 v = tid; v < nd; v += kSThreads) {
@@ -551,22 +663,30 @@ __global__ void __launch_bounds__(kSThreads) k_scatter(Job j, int level) {
       }
       tcount[v] = run;
       tbase[v] = run;
+      // publish this tile's count at once: later tiles of the bin may be waiting for it
+      if (j.wide) lb_publish<u64>((u64*)j.status[L], status_off + tib * nd + v, tib, run);
+      else lb_publish<u32>((u32*)j.status[L], status_off + tib * nd + v, tib, run);
     }
     __syncthreads();
-    block_exclusive_scan<kSThreads>(tbase, nd, scan_scr);
-    // decoupled look-back over the earlier tiles of this bin
-    for (u32 v = tid; v < nd; v += kSThreads) {
-      const u64 self = status_off + tib * nd + v;
-      const bool stall = j.inject && v == 0 && tib == 1;
-      const u64 excl = j.wide ? look_back<u64>((u64*)j.status[L], self, nd, tib, tcount[v], j, stall)
-                              : look_back<u32>((u32*)j.status[L], self, nd, tib, tcount[v], j, stall);
-      gbase[v] = begin + bbase[v] + excl - tbase[v];
-    }
+    if (j.wide) tile_offsets<u64, kDigitsPerThread>((u64*)j.status[L], status_off, tib, nd, tcount, tbase, scan_scr, mybase, begin, size, j, gbase);
+    else tile_offsets<u32, kDigitsPerThread>((u32*)j.status[L], status_off, tib, nd, tcount, tbase, scan_scr, mybase, begin, size, j, gbase);
+    if (cnt == T) {
 #pragma unroll
-    for (int it = 0; it < IT; it++) {
-      if (packed[it] != 0xffffffffu) {
+      for (int it = 0; it < IT; it++) {
         const u32 d = packed[it] >> 16;
-        perm[tbase[d] + wh[d] + (packed[it] & 0xffffu)] = (u16)(warp * PW + it * 32 + lane);
+        const u32 slot = tbase[d] + wh[d] + (packed[it] & 0xffffu);
+        perm[slot] = (u16)(warp * PW + it * 32 + lane);
+        sdig[slot] = (u16)d;
+      }
+    } else {
+#pragma unroll
+      for (int it = 0; it < IT; it++) {
+        if (packed[it] != 0xffffffffu) {
+          const u32 d = packed[it] >> 16;
+          const u32 slot = tbase[d] + wh[d] + (packed[it] & 0xffffu);
+          perm[slot] = (u16)(warp * PW + it * 32 + lane);
+          sdig[slot] = (u16)d;
+        }
       }
     }
     __syncthreads();
@@ -575,33 +695,23 @@ __global__ void __launch_bounds__(kSThreads) k_scatter(Job j, int level) {
 #pragma unroll
       for (int w = 0; w < kSWarps; w++) whist[w * WS + v] = 0;
     }
-    // write the tile in digit order: consecutive slots of one digit go to consecutive
-    // records.  A destination outside the bin (possible only after a failed wait or a
-    // corrupted histogram, both reported) is skipped, never written.
-    const u64 hi_rec = begin + size;
-    bool bad = false;
+    // write the tile in digit order: consecutive slots of one digit go to consecutive records
     if (RW == 2) {
       for (u32 s = tid; s < cnt; s += kSThreads) {
-        const u32 r = perm[s];
-        const ulonglong2 v = *reinterpret_cast<const ulonglong2*>(stage + 2 * r);
-        Key<KW> k;
-        k.w[0] = v.x & j.keymask[0];
-        if (KW == 2) k.w[KW - 1] = v.y & j.keymask[1];
-        const u64 dst = gbase[digit_of<KW>(k, lo, W)] + s;
-        if (dst < begin || dst >= hi_rec) { bad = true; continue; }
-        __stcs(reinterpret_cast<ulonglong2*>(dstb + 2 * dst), v);
+        const u64 g = gbase[sdig[s]];
+        if (g == kSkip) continue;
+        const ulonglong2 v = *reinterpret_cast<const ulonglong2*>(stage + 2 * (u32)perm[s]);
+        __stcs(reinterpret_cast<ulonglong2*>(dstb + 2 * (g + s)), v);
       }
     } else {
       for (u32 s = tid; s < cnt; s += kSThreads) {
-        const u32 r = perm[s];
-        const u64* sp = stage + (u64)r * RW;
-        const u64 dst = gbase[digit_of<KW>(load_key<KW>(sp, j), lo, W)] + s;
-        if (dst < begin || dst >= hi_rec) { bad = true; continue; }
-        u64* d = dstb + dst * RW;
+        const u64 g = gbase[sdig[s]];
+        if (g == kSkip) continue;
+        const u64* sp = stage + (u64)perm[s] * RW;
+        u64* d = dstb + (g + s) * RW;
         for (u32 w = 0; w < RW; w++) __stcs(d + w, sp[w]);
       }
     }
-    if (bad) atomicOr(&ctl->err, kErrInternal);
     __syncthreads();
   }
 }
@@ -716,7 +826,7 @@ __global__ void __launch_bounds__(kThreads) k_classify(Job j, int level) {
     if (tid == 0) {
       // greedy packing of consecutive small sub-bins into on-chip chunks
       u64 cb = 0;
-      u32 csz = 0, nsub = 0;
+      u32 csz = 0, nsub = 0, vfirst = 0, vlast = 0;
       bool open = false, uns = false;
       auto emit = [&]() {
         if (open && (uns || p1)) {
@@ -728,8 +838,13 @@ __global__ void __launch_bounds__(kThreads) k_classify(Job j, int level) {
             ch.begin = bin.begin + cb;
             ch.size = csz;
             ch.flags = (p1 ? kChSrcTmp : 0u) | (uns ? 0u : kChCopyOnly);
-            // one sub-bin shares every bit >= lo; several also differ in the digit itself
-            ch.p = nsub == 1 ? bin.lo : bin.lo + bin.W;
+            // one sub-bin shares every bit >= lo; several differ in the digit itself
+            ch.p = bin.lo;
+            ch.pw = (u16)bin.W;
+            ch.v0 = vfirst;
+            u32 sb = 0;
+            while ((1u << sb) < vlast - vfirst + 1) sb++;
+            ch.sb = (u16)(nsub == 1 ? 0 : sb);
             j.chunks[idx] = ch;
           }
         }
@@ -745,11 +860,13 @@ __global__ void __launch_bounds__(kThreads) k_classify(Job j, int level) {
             cb = boff[v];
             csz = 0;
             nsub = 0;
+            vfirst = v;
             uns = false;
             open = true;
           }
           csz += sz;
           nsub++;
+          vlast = v;
           if (k == 2) uns = true;
         } else {
           emit();

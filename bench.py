@@ -38,6 +38,12 @@ WORKLOADS = {
     "zipf_1e9_r16": ("zipf", 1_000_000_000, 16, 8, 3, "Zipf(1.0) ranks over 2^32 -> seeded bijection to u64, index payload"),
     "kmer_5e8_r24": ("kmer", 500_000_000, 24, 16, 4, "16-byte 64-mer keys, high word from 1,024 prefixes, index payload"),
     "uniform_1e6_r8": ("uniform", 1_000_000, 8, 8, 1, "uniform u64 keys, no payload"),
+    "served_200rps": ("uniform", 64_000_000, 0, 8, 7,
+                      "Poisson arrivals 200/s, sizes log-uniform in [1024, 64e6] records, rec_size in {8,16,32}, "
+                      "uniform u64 keys (seed 7)"),
+    "batched_1e5_r16": ("uniform", 2_000_000_000, 16, 8, 6,
+                        "100,000 segments, log-uniform sizes in [1, 1e6] scaled to sum <= 2e9 (seed 5); uniform u64 "
+                        "keys (seed 6), u64 index payload"),
 }
 
 
@@ -54,6 +60,9 @@ def parse():
     p.add_argument("--no-cpu", action="store_true")
     p.add_argument("--cpu-seconds", type=float, default=12.0, help="CPU oracle sample budget")
     p.add_argument("--profile-out", default=None, help="write per-kernel timing records here (json)")
+    p.add_argument("--duration", type=float, default=60.0, help="served: seconds of arrivals")
+    p.add_argument("--saturate", type=int, default=2000, help="served: requests in the saturated runs")
+    p.add_argument("--cap-gb", type=float, default=120.0, help="served: HBM admission cap")
     p.add_argument("--plan", default="", help="tuning knobs, e.g. digit_bits_max=9,tile_records=2048")
     return p.parse_args()
 
@@ -145,6 +154,23 @@ class ClockSampler:
         return {"sm_mhz": statistics.median(sm), "sm_max_mhz": max(mx), "reasons": sorted(reasons), "samples": len(sm)}
 
 
+def max_over_ranks(x: float, dist=None, device="cpu") -> float:
+    """The slowest rank's time: every rank passes its own, every rank gets the maximum."""
+    if dist is None:
+        return float(x)
+    import torch
+
+    t = torch.tensor([float(x)], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def replica_throughput(n: int, world: int, steps: int, max_ms: float) -> float:
+    """Records/s of the whole job: every rank sorts its own n records per step (replicas,
+    weak scaling), and the job takes as long as its slowest rank."""
+    return n * world * steps / (max_ms / 1e3)
+
+
 def cpu_baseline(kind, n_full, R, K, seed, budget_s):
     """The oracle (single-threaded LSD radix sort) on a bounded sample of the workload."""
     import oracle
@@ -195,10 +221,254 @@ def reference_arm(args):
     return 0
 
 
+def segment_bytes(sizes, R, chunk_max, wmax):
+    """Algorithmic HBM bytes of sorting each segment alone: a segment of at most chunk_max
+    records is read and written once (on-chip sort); a larger one is read once for the first
+    histogram, read and written once per distribution level (each level splits by a digit of
+    up to wmax bits until bins fit on chip), and read and written once by the on-chip pass."""
+    s = np.asarray(sizes, dtype=np.float64)
+    levels = np.where(s > chunk_max, np.ceil(np.log2(np.maximum(s, 1) / chunk_max) / wmax), 0)
+    return float(np.sum(np.where(s > chunk_max, s * R * (1 + 2 * levels + 2), 2 * s * R)))
+
+
+def batched(args):
+    """--workload batched_1e5_r16: 100,000 independent sorts of uneven sizes in one segmented
+    call replayed from a CUDA graph, against one plain radix_sort call per segment on the same
+    data.  Both are stable, so their outputs must agree byte for byte."""
+    import ctypes
+
+    import torch
+
+    import paper_1703_00687_gb300 as rg
+
+    kind, cap, R, K, seed, desc = WORKLOADS[args.workload]
+    if args.n:
+        cap = args.n
+    torch.cuda.set_device(0)
+    dev = torch.device("cuda", 0)
+    sizes = wl.batched_sizes(cap=cap, seed=5).astype(np.int64)
+    offs = np.zeros(len(sizes) + 1, dtype=np.int64)
+    np.cumsum(sizes, out=offs[1:])
+    n = int(offs[-1])
+    h_in = torch.empty((n, R), dtype=torch.uint8, pin_memory=True)
+    wl.make(kind, n, R, K, seed, out=h_in)
+    pristine = h_in.to(dev)
+    buf = torch.empty_like(pristine)
+    tmp = torch.empty_like(pristine)
+    d_offs = torch.from_numpy(offs).to(dev)
+    stream = torch.cuda.Stream(device=dev)
+
+    # batched: one segmented call, captured once and replayed
+    buf.copy_(pristine)
+    launches0 = rg.launch_count()
+    g = rg.SortGraph(buf, K, offsets=d_offs, tmp=tmp, stream=stream)
+    per_replay = (rg.launch_count() - launches0) // 2  # the warm-up call and the captured one
+    for _ in range(max(0, args.warmup - 1)):
+        stream.wait_stream(torch.cuda.current_stream())
+        buf.copy_(pristine)
+        stream.wait_stream(torch.cuda.current_stream())
+        g.replay()
+    torch.cuda.synchronize()
+    ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(args.steps)]
+    with ClockSampler(0) as clk:
+        for a, b in ev:
+            buf.copy_(pristine)  # restore (untimed), on the current stream
+            stream.wait_stream(torch.cuda.current_stream())
+            a.record(stream)
+            g.replay()
+            b.record(stream)
+            torch.cuda.current_stream().wait_stream(stream)
+        torch.cuda.synchronize()
+    if rg.status(stream) != 0:
+        raise SystemExit("device status error in the batched sort")
+    batched_ms = [a.elapsed_time(b) for a, b in ev]
+    got = buf.clone()
+
+    # plain: one radix_sort call per segment, same data, same stream, one step
+    L = rg.lib()
+    buf.copy_(pristine)
+    torch.cuda.synchronize()
+    sp = ctypes.c_void_p(stream.cuda_stream)
+    bp, tp = buf.data_ptr(), tmp.data_ptr()
+    plain_launches0 = rg.launch_count()
+    a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    t0 = time.perf_counter()
+    a.record(stream)
+    for i in range(len(sizes)):
+        o, c = int(offs[i]), int(sizes[i])
+        rc = L.radix_sort(bp + o * R, tp + o * R, c, R, K, sp)
+        if rc != 0:
+            raise SystemExit(f"radix_sort failed on segment {i}: {rc}")
+    b.record(stream)
+    stream.synchronize()
+    plain_wall = time.perf_counter() - t0
+    plain_ms = a.elapsed_time(b)
+    plain_launches = rg.launch_count() - plain_launches0
+    if rg.status(stream) != 0:
+        raise SystemExit("device status error in the plain sorts")
+    same = bool(torch.equal(got, buf))
+    del got
+
+    b_alg = segment_bytes(sizes, R, rg.chunk_records(R), rg.get_plan().get("digit_bits_max") or 9)
+    peak, peak_src = measured_peaks()
+    med = statistics.median(batched_ms)
+    line = {
+        "metric": "records/s", "value": n / (med / 1e3), "unit": "records/s", "n_gpus": 1, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": med, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+        "dtype": "u64", "data": "synthetic",
+        "config": {"workload": args.workload, "n": n, "segments": len(sizes), "rec_size": R, "key_size": K,
+                   "keys": desc, "max_segment": int(sizes.max()), "api": "radix_sort_segmented in a CUDA graph",
+                   "l2": f"input {n * R / 1e9:.0f} GB >> L2; pristine input restored before every step"},
+        "hbm": {"b_alg_bytes": b_alg, "gbs": b_alg / (med / 1e3) / 1e9, "peak": peak, "peak_source": peak_src,
+                "frac": b_alg / (med / 1e3) / 1e9 / peak},
+        "plain": {"value": n / (plain_ms / 1e3), "ms": plain_ms, "wall_s": plain_wall, "launches": plain_launches,
+                  "api": "one radix_sort call per segment on one stream"},
+        "speedup_vs_plain": plain_ms / med, "outputs_identical": same,
+        "gpu_launches": per_replay * args.steps, "step_ms": batched_ms, "clocks": clk.summary(),
+    }
+    print(json.dumps(line), flush=True)
+    return 0 if same else 1
+
+
+def served(args):
+    """--workload served_200rps: a stream of sort requests (Poisson arrivals, log-uniform sizes,
+    mixed record sizes) through the continuous-batching server, against the same requests
+    sorted one at a time with plain calls (copy in, sort, copy out, wait).  Each mode runs
+    twice: paced by the arrival times (latency p50/p99 from arrival to result on the host) and
+    saturated (the first --saturate requests all arrive at once: aggregate records/s)."""
+    import torch
+
+    import paper_1703_00687_gb300 as rg
+    from paper_1703_00687_gb300.serve import Server, percentile
+
+    _, hi, _, K, seed, desc = WORKLOADS[args.workload]
+    torch.cuda.set_device(0)
+    dev = torch.device("cuda", 0)
+    rate = 200.0
+    m = max(1, int(args.duration * rate * 1.2) + 64)
+    gaps = wl.exponential(m, rate, seed)
+    t_arr = np.cumsum(gaps)
+    m = int(np.searchsorted(t_arr, args.duration))
+    t_arr = t_arr[:m]
+    sizes = wl.log_uniform(m, 1024, hi, seed).astype(np.int64)
+    recs = np.array([8, 16, 32], dtype=np.int64)[wl.uniform_below(m, 3, seed).astype(np.int64)]
+    # request data: windows of one pinned pool of uniform random words (every window's keys
+    # are uniform); a request of n records of R bytes is n*R consecutive pool bytes
+    pool_bytes = int(hi * 32 * 2)
+    pool = torch.empty(pool_bytes, dtype=torch.uint8, pin_memory=True)
+    wl.make("uniform", pool_bytes // 8, 8, 8, seed, out=pool.view(-1, 8))
+    starts = wl.uniform_below(m, pool_bytes // 8 - hi * 4, seed, stream=9).astype(np.int64) * 8
+
+    def req(i):
+        n, R = int(sizes[i]), int(recs[i])
+        o = int(starts[i])
+        return pool[o:o + n * R].view(n, R)
+
+    # serial plain calls: one request at a time on one stream
+    d_in = torch.empty(hi * 32, dtype=torch.uint8, device=dev)
+    d_tmp = torch.empty_like(d_in)
+    h_out = torch.empty(hi * 32, dtype=torch.uint8, pin_memory=True)
+    stream = torch.cuda.Stream(device=dev)
+    for R in (8, 16, 32):
+        rg.reserve(hi, R, K, 0, stream=stream)
+
+    def serial(idx, paced):
+        lat, t0 = [], time.perf_counter()
+        with torch.cuda.stream(stream):
+            for i in idx:
+                if paced:
+                    wait = t0 + t_arr[i] - time.perf_counter()
+                    if wait > 0:
+                        time.sleep(wait)
+                arr = t0 + t_arr[i] if paced else t0
+                h = req(i)
+                n, R = h.shape
+                d = d_in[:n * R].view(n, R)
+                d.copy_(h, non_blocking=True)
+                rg.sort(d, K, tmp=d_tmp[:n * R].view(n, R), stream=stream)
+                h_out[:n * R].view(n, R).copy_(d, non_blocking=True)
+                stream.synchronize()
+                lat.append(time.perf_counter() - arr)
+        return lat, time.perf_counter() - t0
+
+    def server(idx, paced):
+        with Server(cap_bytes=int(args.cap_gb * 1e9), device=dev) as srv:
+            for R in (8, 16, 32):  # reserve every lane's workspace before the clock starts
+                for ln in srv.lanes:
+                    srv._reserve(ln, R, K)
+            torch.cuda.synchronize()
+            t0 = time.perf_counter()
+            left = [len(idx)]
+            all_done = threading.Event()
+            errors = []
+            mu = threading.Lock()
+
+            def finished(f):  # drop the result at once: the bench keeps no outputs
+                with mu:
+                    if f.exception() is not None:
+                        errors.append(f.exception())
+                    left[0] -= 1
+                    if left[0] == 0:
+                        all_done.set()
+
+            for i in idx:
+                if paced:
+                    wait = t0 + t_arr[i] - time.perf_counter()
+                    if wait > 0:
+                        time.sleep(wait)
+                srv.submit(req(i), K, arrival=t0 + t_arr[i] if paced else t0).add_done_callback(finished)
+            all_done.wait()
+            t1 = time.perf_counter()
+            if errors:
+                raise errors[0]
+            lat = [done - arr for (_, _, arr, _, done) in srv.completed]
+            info = {"groups": srv.groups, "peak_in_use_gb": srv.peak_in_use / 1e9}
+        return lat, t1 - t0, info
+
+    # one warm-up pass of a few requests through both paths
+    warm = list(range(min(m, 16)))
+    serial(warm, False)
+    server(warm, False)
+    sat = list(range(min(m, args.saturate)))
+    sat_records = int(sizes[sat].sum())
+    with ClockSampler(0) as clk:
+        s_lat, s_wall = serial(list(range(m)), True)
+        v_lat, v_wall, v_info = server(list(range(m)), True)
+        s_sat_lat, s_sat_wall = serial(sat, False)
+        v_sat_lat, v_sat_wall, v_sat_info = server(sat, False)
+    total = int(sizes.sum())
+    pct = lambda xs, q: 1e3 * percentile(xs, q)  # noqa: E731
+    line = {
+        "metric": "records/s", "value": sat_records / v_sat_wall, "unit": "records/s", "n_gpus": 1,
+        "steps": 1, "warmup": 1, "ms_per_step": 1e3 * v_sat_wall, "higher_is_better": True, "scaling": "weak",
+        "vs_baseline": None, "dtype": "u64", "data": "synthetic",
+        "config": {"workload": args.workload, "requests": m, "duration_s": args.duration, "keys": desc,
+                   "records_total": total, "bytes_total": int((sizes * recs).sum()), "cap_gb": args.cap_gb,
+                   "saturated_requests": len(sat), "api": "serve.Server (host in, host out)"},
+        "latency_ms": {"p50": pct(v_lat, 50), "p99": pct(v_lat, 99), "serial_p50": pct(s_lat, 50),
+                       "serial_p99": pct(s_lat, 99)},
+        "paced": {"server_records_per_s": total / v_wall, "serial_records_per_s": total / s_wall,
+                  "server": v_info},
+        "saturated": {"server_records_per_s": sat_records / v_sat_wall, "serial_records_per_s": sat_records / s_sat_wall,
+                      "server_p99_ms": pct(v_sat_lat, 99), "serial_p99_ms": pct(s_sat_lat, 99),
+                      "server": v_sat_info},
+        "e2e": {"value": sat_records / v_sat_wall, "unit": "records/s",
+                "h2d_bytes_per_step": int((sizes[sat] * recs[sat]).sum()),
+                "d2h_bytes_per_step": int((sizes[sat] * recs[sat]).sum())},
+        "clocks": clk.summary(),
+    }
+    print(json.dumps(line), flush=True)
+    return 0
+
+
 def main():
     args = parse()
     if args.impl == "reference":
         return reference_arm(args)
+    if args.workload.startswith("batched"):
+        return batched(args)
+    if args.workload.startswith("served"):
+        return served(args)
     import torch
 
     import paper_1703_00687_gb300 as rg
@@ -258,12 +528,8 @@ def main():
     if st != 0:
         raise SystemExit(f"device status error {st} during the timed steps")
     step_ms = [a.elapsed_time(b) for a, b in ev]
-    tot_ms = sum(step_ms)
-    if dist:
-        t = torch.tensor([tot_ms], device=dev)
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        tot_ms = float(t.item())
-    value = n * world * args.steps / (tot_ms / 1e3)
+    tot_ms = max_over_ranks(sum(step_ms), dist, dev)
+    value = replica_throughput(n, world, args.steps, tot_ms)
 
     # per-kernel shares and the dominant kernel's roofline (CUDA events on the launch stream)
     per = {}
@@ -312,11 +578,7 @@ def main():
             t0 = time.perf_counter()
             rg.sort_host(h_in, K, h_out=h_out, d_buf=buf, d_tmp=tmp)
             times.append(time.perf_counter() - t0)
-        et = sum(times)
-        if dist:
-            t = torch.tensor([et], device=dev)
-            dist.all_reduce(t, op=dist.ReduceOp.MAX)
-            et = float(t.item())
+        et = max_over_ranks(sum(times), dist, dev)
         e2e = {"value": n * world * len(times) / et, "unit": "records/s", "h2d_bytes_per_step": n * R,
                "d2h_bytes_per_step": n * R, "ms_per_step": 1e3 * et / len(times), "api": "sort_host (pinned)"}
 

@@ -139,6 +139,29 @@ rs_status radix_sort_get_plan(rs_plan *plan);
 uint64_t radix_sort_launch_count(void);
 
 /*
+ * Largest bin (in records of rec_size bytes) that the current plan sorts in one on-chip
+ * pass: bins and segments up to this size skip the distribution levels.  0 for an invalid
+ * rec_size.  Host only; no GPU needed.
+ */
+uint32_t radix_sort_chunk_records(uint32_t rec_size);
+
+/*
+ * Bytes of the library-owned workspace that a call of n records (n_segs segments; 0 for
+ * radix_sort) needs under the current plan; 0 for invalid sizes.  Host only.
+ */
+uint64_t radix_sort_workspace_bytes(uint64_t n, uint32_t rec_size, uint32_t key_size, uint64_t n_segs);
+
+/*
+ * Makes the workspace of (current device, stream) large enough for calls of up to n records
+ * and n_segs segments, so that later calls of that size neither allocate nor synchronise
+ * (growing a workspace drains its stream and frees the old one; cudaMalloc and cudaFree can
+ * stall every stream of the device).  Call it before capturing a stream into a CUDA graph.
+ * Returns RS_ERR_NO_MEMORY if the allocation fails, RS_ERR_INVALID_ARG for a bad layout.
+ */
+rs_status radix_sort_reserve(uint64_t n, uint32_t rec_size, uint32_t key_size, uint64_t n_segs,
+                             rs_stream_t stream);
+
+/*
  * Per-launch timing (for benchmarks).  radix_sort_profile(1) starts a session: every kernel
  * the library launches from then on is bracketed by two CUDA events recorded on the
  * launching stream; radix_sort_profile(0) stops recording.  radix_sort_profile_read() waits

@@ -17,7 +17,8 @@ import ctypes
 from ._lib import KERNEL_NAMES, RadixSortError, RsKernelTime, RsPlan, check, lib
 
 __all__ = ["sort", "sort_host", "sort_segmented", "partition", "histogram", "status", "release", "set_plan",
-           "get_plan", "launch_count", "profile", "RadixSortError", "lib"]
+           "get_plan", "launch_count", "chunk_records", "workspace_bytes", "reserve",
+           "profile", "RadixSortError", "lib", "SortGraph"]
 
 
 def _torch():
@@ -160,6 +161,21 @@ def launch_count() -> int:
     return int(lib().radix_sort_launch_count())
 
 
+def workspace_bytes(n: int, rec_size: int, key_size: int, n_segs: int = 0) -> int:
+    """Library workspace bytes a call of n records (n_segs segments) needs under the plan."""
+    return int(lib().radix_sort_workspace_bytes(n, rec_size, key_size, n_segs))
+
+
+def reserve(n: int, rec_size: int, key_size: int, n_segs: int = 0, stream=None) -> None:
+    """Pre-allocates the workspace of ``stream`` for calls of up to n records / n_segs segments."""
+    check(lib().radix_sort_reserve(n, rec_size, key_size, n_segs, _stream(stream)), "radix_sort_reserve")
+
+
+def chunk_records(rec_size: int) -> int:
+    """Largest bin (records) the current plan sorts in one on-chip pass."""
+    return int(lib().radix_sort_chunk_records(rec_size))
+
+
 class profile:
     """Context manager: per-kernel CUDA-event timings of the library's launches.
 
@@ -182,3 +198,6 @@ class profile:
         self.records = [(KERNEL_NAMES.get(buf[i].kernel, str(buf[i].kernel)), buf[i].level, buf[i].ms)
                         for i in range(got)]
         return False
+
+
+from .graph import SortGraph  # noqa: E402

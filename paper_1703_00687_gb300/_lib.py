@@ -44,6 +44,9 @@ SIGNATURES = {
     "radix_sort_set_plan": (_i32, [ctypes.POINTER(RsPlan)]),
     "radix_sort_get_plan": (_i32, [ctypes.POINTER(RsPlan)]),
     "radix_sort_launch_count": (_u64, []),
+    "radix_sort_chunk_records": (_u32, [_u32]),
+    "radix_sort_workspace_bytes": (_u64, [_u64, _u32, _u32, _u64]),
+    "radix_sort_reserve": (_i32, [_u64, _u32, _u32, _u64, _vp]),
     "radix_sort_test_inject": (_i32, [_u32]),
     "radix_sort_noalloc": (_i32, [_vp, _vp, _u64, _u32, _u32, _vp, _vp]),
     "radix_sort_profile": (_i32, [_i32]),

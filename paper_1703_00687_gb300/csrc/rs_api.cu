@@ -20,6 +20,8 @@
 namespace rsg {
 
 u32 chunk_capacity(u32 RW);
+size_t level_smem_for(u32 T, u32 RW, u32 KW, u32 wmax);
+constexpr size_t kMaxSmemPerCta = 227 * 1024;
 
 struct Workspace {
   void* mem = nullptr;
@@ -72,6 +74,33 @@ static Caps caps_for(u64 n, u32 T, u32 cm, u32 wmax, bool wide, u64 n_segs) {
   c.off_tiles = o; o = al(o + c.tiles * 4);
   c.bytes = o;
   return c;
+}
+
+// Tile size, on-chip limit, digit width and look-back word size of a job under a plan.
+struct Shape {
+  u32 T, chunk_max, wmax;
+  bool wide;
+};
+
+static Shape shape_for(u64 n, u32 rec_size, u32 key_size, const rs_plan& p) {
+  Shape sh;
+  sh.wmax = p.digit_bits_max ? p.digit_bits_max : 9;
+  u32 T = 4096;  // 64 KB of 16-byte records per tile (measured best of 1024..4096)
+  while (T > 256 && (u64)T * rec_size > 65536) T >>= 1;
+  if (p.tile_records) T = p.tile_records;
+  // a planned tile too large for one CTA's shared memory is halved until it fits
+  const u32 KW = key_size > 8 ? 2 : 1;
+  while (T > 256 && level_smem_for(T, rec_size / 8, KW, sh.wmax) > kMaxSmemPerCta) T >>= 1;
+  sh.T = T;
+  const u32 cap = chunk_capacity(rec_size / 8);
+  sh.chunk_max = p.chunk_records && p.chunk_records < cap ? p.chunk_records : cap;
+  sh.wide = n >= (1ull << 30);  // 64-bit look-back words for bins of 2^30 records or more
+  return sh;
+}
+
+static rs_plan current_plan() {
+  std::lock_guard<std::mutex> lk(g_mu);
+  return g_plan;
 }
 
 static rs_status get_workspace(int dev, cudaStream_t s, size_t bytes, Workspace** out) {
@@ -163,21 +192,14 @@ static rs_status setup_job(void* in, void* tmp, u64 n, u32 rec_size, u32 key_siz
     const int bytes = (int)key_size - 8 * (int)w;
     j.keymask[w] = bytes >= 8 ? ~0ull : bytes <= 0 ? 0ull : ((1ull << (8 * bytes)) - 1);
   }
-  rs_plan p;
-  {
-    std::lock_guard<std::mutex> lk(g_mu);
-    p = g_plan;
-  }
-  j.wmax = p.digit_bits_max ? p.digit_bits_max : 9;
-  u32 T = 4096;  // 64 KB of 16-byte records per tile (measured best of 1024..4096)
-  while (T > 256 && (u64)T * rec_size > 65536) T >>= 1;
-  if (p.tile_records) T = p.tile_records;
-  j.T = T;
-  const u32 cap = chunk_capacity(j.RW);
-  j.chunk_max = p.chunk_records && p.chunk_records < cap ? p.chunk_records : cap;
+  const rs_plan p = current_plan();
+  const Shape sh = shape_for(n, rec_size, key_size, p);
+  j.wmax = sh.wmax;
+  j.T = sh.T;
+  j.chunk_max = sh.chunk_max;
   j.watchdog = p.watchdog_polls ? p.watchdog_polls : (1u << 16);
   j.inject = g_inject.exchange(0);
-  j.wide = n >= (1ull << 30) ? 1u : 0u;  // 64-bit look-back words for bins of 2^30 records or more
+  j.wide = sh.wide ? 1u : 0u;
   j.n_segs = n_segs;
   Caps c = caps_for(n, j.T, j.chunk_max, j.wmax, j.wide != 0, n_segs);
   Workspace* w = nullptr;
@@ -320,20 +342,13 @@ static rs_status noalloc_setup(void* in, void* tmp, u64 n, u32 rec_size, u32 key
     const int bytes = (int)key_size - 8 * (int)w;
     j.keymask[w] = bytes >= 8 ? ~0ull : bytes <= 0 ? 0ull : ((1ull << (8 * bytes)) - 1);
   }
-  rs_plan p;
-  {
-    std::lock_guard<std::mutex> lk(g_mu);
-    p = g_plan;
-  }
-  j.wmax = p.digit_bits_max ? p.digit_bits_max : 9;
-  u32 T = 4096;
-  while (T > 256 && (u64)T * rec_size > 65536) T >>= 1;
-  if (p.tile_records) T = p.tile_records;
-  j.T = T;
-  const u32 cap = chunk_capacity(j.RW);
-  j.chunk_max = p.chunk_records && p.chunk_records < cap ? p.chunk_records : cap;
+  const rs_plan p = current_plan();
+  const Shape sh = shape_for(n, rec_size, key_size, p);
+  j.wmax = sh.wmax;
+  j.T = sh.T;
+  j.chunk_max = sh.chunk_max;
   j.watchdog = p.watchdog_polls ? p.watchdog_polls : (1u << 16);
-  j.wide = n >= (1ull << 30) ? 1u : 0u;
+  j.wide = sh.wide ? 1u : 0u;
   const Caps c = caps_for(n, j.T, j.chunk_max, j.wmax, j.wide != 0, 0);
   if (c.bytes > kNoAllocBytes) return RS_ERR_TOO_LARGE;
   st->c = c;
@@ -501,11 +516,14 @@ rs_status radix_sort_status(rs_stream_t stream) {
     if (it == g_ws.end() || !it->second.mem) return RS_OK;
     ctl = it->second.ctl;
   }
+  // read and clear the word on the stream itself, so no other stream of the device waits
   u32 err = 0;
-  if (cudaMemcpy(&err, &ctl->err, sizeof err, cudaMemcpyDeviceToHost) != cudaSuccess) return RS_ERR_CUDA;
+  if (cudaMemcpyAsync(&err, &ctl->err, sizeof err, cudaMemcpyDeviceToHost, s) != cudaSuccess ||
+      cudaStreamSynchronize(s) != cudaSuccess)
+    return RS_ERR_CUDA;
   if (err) {
-    u32 zero = 0;
-    cudaMemcpy(&ctl->err, &zero, sizeof zero, cudaMemcpyHostToDevice);
+    if (cudaMemsetAsync(&ctl->err, 0, sizeof(u32), s) != cudaSuccess || cudaStreamSynchronize(s) != cudaSuccess)
+      return RS_ERR_CUDA;
   }
   if (err & kErrTimeout) return RS_ERR_DEVICE_TIMEOUT;
   if (err & kErrOverflow) return RS_ERR_QUEUE_OVERFLOW;
@@ -564,6 +582,29 @@ rs_status radix_sort_get_plan(rs_plan* plan) {
 }
 
 uint64_t radix_sort_launch_count(void) { return (uint64_t)g_launches.load(); }
+
+uint32_t radix_sort_chunk_records(uint32_t rec_size) {
+  if (rec_size == 0 || rec_size % 8 != 0 || rec_size > 256) return 0;
+  return shape_for(1, rec_size, 8, current_plan()).chunk_max;
+}
+
+uint64_t radix_sort_workspace_bytes(uint64_t n, uint32_t rec_size, uint32_t key_size, uint64_t n_segs) {
+  if (validate_layout(rec_size, key_size) != RS_OK || n > UINT64_MAX / rec_size) return 0;
+  const Shape sh = shape_for(n, rec_size, key_size, current_plan());
+  return (uint64_t)caps_for(n, sh.T, sh.chunk_max, sh.wmax, sh.wide, n_segs).bytes;
+}
+
+rs_status radix_sort_reserve(uint64_t n, uint32_t rec_size, uint32_t key_size, uint64_t n_segs, rs_stream_t stream) {
+  rs_status r = validate_layout(rec_size, key_size);
+  if (r != RS_OK) return r;
+  if (n > UINT64_MAX / rec_size) return RS_ERR_TOO_LARGE;
+  int dev = 0;
+  if (cudaGetDevice(&dev) != cudaSuccess) return RS_ERR_CUDA;
+  const Shape sh = shape_for(n, rec_size, key_size, current_plan());
+  const Caps c = caps_for(n, sh.T, sh.chunk_max, sh.wmax, sh.wide, n_segs);
+  Workspace* w = nullptr;
+  return get_workspace(dev, (cudaStream_t)stream, c.bytes, &w);
+}
 
 rs_status radix_sort_profile(int enable) {
   std::lock_guard<std::mutex> lk(g_prof_mu);

@@ -517,7 +517,7 @@ constexpr u64 kSkip = ~0ull;  // gbase of a digit whose run would leave its bin
 
 // Turns the tile's digit counts into destinations: the exclusive scan over digits (tbase) and,
 // per digit, the records of that digit in the bin's earlier tiles (decoupled look-back).  The
-// first look-back words are read before the scan so that the scan hides their round trip.  A
+// first look-back words of all of a thread's digits are read together (one round trip).  A
 // digit run that would leave the bin (possible only after a failed wait or a corrupted
 // histogram) gets kSkip and is not written.
 template <typename S, u32 Q>
@@ -906,6 +906,12 @@ __global__ void k_read_counts(Job j, u64* out, u32 nd) {
 
 // ------------------------------------------------------------------- launchers
 size_t scatter_smem_bytes(const Job& j) { return scatter_layout(j.T, j.RW, j.wmax).total; }
+
+// Largest shared memory either level kernel needs for tiles of T records.
+size_t level_smem_for(u32 T, u32 RW, u32 KW, u32 wmax) {
+  const size_t a = scatter_layout(T, RW, wmax).total, b = hist_smem_bytes_for(T, KW);
+  return a > b ? a : b;
+}
 
 template <int KW, int RWT, int IT>
 static cudaError_t launch_scatter_t(const Job& j, int level, u32 grid, cudaStream_t s, int* occ) {

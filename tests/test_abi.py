@@ -100,3 +100,17 @@ def test_inject_flag_validation():
     L = rg.lib()
     assert L.radix_sort_test_inject(2) == 1
     assert L.radix_sort_test_inject(0) == 0
+
+
+def test_chunk_records_follows_the_plan_and_rejects_bad_sizes():
+    assert rg.chunk_records(7) == 0 and rg.chunk_records(0) == 0 and rg.chunk_records(264) == 0
+    default16, default8 = rg.chunk_records(16), rg.chunk_records(8)
+    assert default16 >= 1024 and default8 >= default16  # smaller records: more fit on chip
+    old = rg.get_plan()
+    try:
+        rg.set_plan(**{**old, "chunk_records": 1000})
+        assert rg.chunk_records(16) == 1000
+        rg.set_plan(**{**old, "chunk_records": 10 ** 9})  # above the capacity: capped
+        assert rg.chunk_records(16) == default16
+    finally:
+        rg.set_plan(**old)

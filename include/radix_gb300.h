@@ -20,16 +20,16 @@
  *
  * Memory.  All record buffers are device memory owned by the caller; the library never
  * allocates, frees or keeps them.  The library owns a metadata workspace per (device,
- * stream) — histograms, bucket bases, bin and chunk lists, look-back words, a status word —
+ * stream) — histograms, bucket bases, per-segment run starts, bin and chunk lists, a status word —
  * allocated on first use with cudaMalloc (so the first call for a given size must not be
  * made while the stream is being captured into a CUDA graph), grown when a larger call
  * needs it, reused, and freed by radix_sort_release().
  *
  * Asynchrony.  Every call validates its arguments on the host and returns at once; the
  * work runs asynchronously on `stream` (NULL = the legacy default stream).  Errors found on
- * the device (a look-back wait that hit its limit, a list that overflowed) set the status
- * word and are reported by radix_sort_status() after the stream has drained; no kernel
- * traps or waits without a bound.  Calls on one stream run in order; calls on different
+ * the device (a list that overflowed, a destination that failed its range check) set the
+ * status word and are reported by radix_sort_status() after the stream has drained; no
+ * kernel traps, and no kernel waits for another CTA (the path has no spin-waits).  Calls on one stream run in order; calls on different
  * streams use different workspaces and may overlap.
  *
  * Errors.  A call that returns anything but RS_OK launched no work.
@@ -54,7 +54,7 @@ typedef enum rs_status {
   RS_ERR_TOO_LARGE = 4,      /* n * rec_size does not fit in 64 bits / in the address space */
   RS_ERR_NO_MEMORY = 5,      /* the workspace could not be allocated */
   RS_ERR_CUDA = 6,           /* a CUDA runtime call failed (launch, memcpy, sync) */
-  RS_ERR_DEVICE_TIMEOUT = 7, /* a device-side wait hit its limit (result undefined) */
+  RS_ERR_DEVICE_TIMEOUT = 7, /* reserved (the path has no device-side waits) */
   RS_ERR_QUEUE_OVERFLOW = 8, /* a device-side list overflowed (result undefined) */
   RS_ERR_UNSUPPORTED = 9,    /* a valid request this build does not handle (key_size > 16) */
   RS_ERR_INTERNAL = 10       /* a device-side consistency check failed (result undefined) */
@@ -129,7 +129,7 @@ typedef struct rs_plan {
   uint32_t tile_records;    /* records per distribution tile: 256, 512, 1024, 2048 or 4096 */
   uint32_t chunk_records;   /* largest bin sorted on chip: 64.. the shared-memory maximum */
   uint32_t sm_limit;        /* use at most this many SMs for the persistent grids */
-  uint32_t watchdog_polls;  /* polls of a look-back wait before it gives up */
+  uint32_t watchdog_polls;  /* reserved, ignored (the path has no device-side waits) */
 } rs_plan;
 
 rs_status radix_sort_set_plan(const rs_plan *plan);
@@ -203,13 +203,13 @@ int64_t radix_sort_profile_read(rs_kernel_time *out, int64_t max);
  * Arguments and result are those of radix_sort; the sort is the same (byte-identical
  * output).  Additionally:
  *   d_status  optional DEVICE pointer to one uint32: when the call's work has run it holds
- *             the call's device-side status (0 = ok; nonzero = a bounded wait gave up or a
- *             range check failed, as radix_sort_status reports for radix_sort).  NULL: none.
+ *             the call's device-side status (0 = ok; nonzero = a list overflowed or a range
+ *             check failed, as radix_sort_status reports for radix_sort).  NULL: none.
  *             (radix_sort_status does not see calls made through this entry point.)
  * Limits:
  *   The workspace needed for (n, rec_size, key_size) must fit the 64 MiB array, else the
  *   call returns RS_ERR_TOO_LARGE and launches nothing.  With the default plan that is about
- *   4.0 x 10^7 records of 16 bytes (8-byte keys), 5.1 x 10^7 of 8 bytes, 2.5 x 10^7 of
+ *   4.0 x 10^7 records of 16 bytes (8-byte keys), 5.9 x 10^7 of 8 bytes, 2.8 x 10^7 of
  *   24 bytes (16-byte keys).
  * Sharing:
  *   Every call uses the same array, on every stream.  Calls whose work overlaps on the GPU
@@ -225,10 +225,10 @@ rs_status radix_sort_noalloc(void *in, void *tmp, uint64_t n, uint32_t rec_size,
                              uint32_t *d_status, rs_stream_t stream);
 
 /*
- * Testing only.  flags = 1: in the next call, the first look-back wait of each distribution
- * pass waits on a device word that nothing writes, so the bounded wait must give up:
- * the call completes, its result is undefined, and radix_sort_status() reports
- * RS_ERR_DEVICE_TIMEOUT.  The flag applies to one call.  flags = 0 clears it.
+ * Testing only.  flags = 1: in the next call, each distribution pass treats the first
+ * non-empty digit run of its first tile as failing the destination range check, so that run
+ * is not written: the call completes, its result is undefined, and radix_sort_status()
+ * reports RS_ERR_INTERNAL.  The flag applies to one call.  flags = 0 clears it.
  */
 rs_status radix_sort_test_inject(uint32_t flags);
 

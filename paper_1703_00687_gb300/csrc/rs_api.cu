@@ -47,39 +47,36 @@ static int sm_count(int dev) {
 
 // Sizes of every workspace region for a job.
 struct Caps {
-  u64 bins, base, status, chunks, pieces, tiles;
+  u64 bins, base, seg, chunks, pieces;
   size_t bytes;
-  size_t off_ctl, off_bins0, off_bins1, off_base0, off_base1, off_status, off_chunks, off_pieces, off_tiles;
+  size_t off_ctl, off_bins0, off_bins1, off_base0, off_base1, off_seg, off_chunks, off_pieces;
 };
 
 static size_t al(size_t x) { return (x + 255) & ~(size_t)255; }
 
-static Caps caps_for(u64 n, u32 T, u32 cm, u32 wmax, bool wide, u64 n_segs) {
+static Caps caps_for(u64 n, u32 cm, u32 wmax, u64 n_segs) {
   Caps c;
-  c.bins = n / ((u64)cm + 1) + 2;
+  c.bins = n / ((u64)cm + 1) + 2;  // large bins of one level (each holds > cm records)
   c.base = 256ull * c.bins + 2 * (n / cm) + (1ull << wmax) + 64;
-  c.status = (n / T + c.bins) * (1ull << wmax) + 64;
+  c.seg = kMaxLanes + c.bins;       // (lane, bin) segments of one level
   c.chunks = 6 * (n / cm) + n_segs + 16;
   c.pieces = n / kPieceRecords + n / ((u64)cm + 1) + 16;
-  c.tiles = n / T + c.bins + 16;
   size_t o = 0;
   c.off_ctl = o; o = al(o + sizeof(Ctl));
   c.off_bins0 = o; o = al(o + c.bins * sizeof(Bin));
   c.off_bins1 = o; o = al(o + c.bins * sizeof(Bin));
   c.off_base0 = o; o = al(o + c.base * 8);
   c.off_base1 = o; o = al(o + c.base * 8);
-  c.off_status = o; o = al(o + c.status * (wide ? 8 : 4));
+  c.off_seg = o; o = al(o + (c.seg << wmax) * 8);
   c.off_chunks = o; o = al(o + c.chunks * sizeof(Chunk));
   c.off_pieces = o; o = al(o + c.pieces * sizeof(Piece));
-  c.off_tiles = o; o = al(o + c.tiles * 4);
   c.bytes = o;
   return c;
 }
 
-// Tile size, on-chip limit, digit width and look-back word size of a job under a plan.
+// Tile size, on-chip limit and digit width of a job under a plan.
 struct Shape {
   u32 T, chunk_max, wmax;
-  bool wide;
 };
 
 static Shape shape_for(u64 n, u32 rec_size, u32 key_size, const rs_plan& p) {
@@ -94,7 +91,7 @@ static Shape shape_for(u64 n, u32 rec_size, u32 key_size, const rs_plan& p) {
   sh.T = T;
   const u32 cap = chunk_capacity(rec_size / 8);
   sh.chunk_max = p.chunk_records && p.chunk_records < cap ? p.chunk_records : cap;
-  sh.wide = n >= (1ull << 30);  // 64-bit look-back words for bins of 2^30 records or more
+  (void)n;
   return sh;
 }
 
@@ -134,6 +131,12 @@ static rs_status get_workspace(int dev, cudaStream_t s, size_t bytes, Workspace*
   }
   *out = &w;
   return RS_OK;
+}
+
+// Tile ranges of a level: one per histogram CTA that fits on the GPU at once.
+static u32 lanes_for(const Job& j, int sms) {
+  const u64 l = (u64)sms * (u64)hist_ctas_per_sm(j);
+  return (u32)(l < 1 ? 1 : l > kMaxLanes ? kMaxLanes : l);
 }
 
 struct Setup {
@@ -197,11 +200,12 @@ static rs_status setup_job(void* in, void* tmp, u64 n, u32 rec_size, u32 key_siz
   j.wmax = sh.wmax;
   j.T = sh.T;
   j.chunk_max = sh.chunk_max;
-  j.watchdog = p.watchdog_polls ? p.watchdog_polls : (1u << 16);
   j.inject = g_inject.exchange(0);
-  j.wide = sh.wide ? 1u : 0u;
   j.n_segs = n_segs;
-  Caps c = caps_for(n, j.T, j.chunk_max, j.wmax, j.wide != 0, n_segs);
+  int sms = sm_count(dev);
+  if (p.sm_limit && (int)p.sm_limit < sms) sms = (int)p.sm_limit;
+  j.lanes = lanes_for(j, sms);
+  Caps c = caps_for(n, j.chunk_max, j.wmax, n_segs);
   Workspace* w = nullptr;
   rs_status r = get_workspace(dev, stream, c.bytes, &w);
   if (r != RS_OK) return r;
@@ -213,18 +217,14 @@ static rs_status setup_job(void* in, void* tmp, u64 n, u32 rec_size, u32 key_siz
   j.base[0] = (u64*)(base + c.off_base0);
   j.base[1] = (u64*)(base + c.off_base1);
   j.cap_base = c.base;
-  j.status[0] = j.status[1] = base + c.off_status;
-  j.cap_status = c.status;
+  j.seg = (u64*)(base + c.off_seg);
+  j.cap_seg = c.seg;
   j.chunks = (Chunk*)(base + c.off_chunks);
   j.cap_chunks = c.chunks;
   j.pieces = (Piece*)(base + c.off_pieces);
   j.cap_pieces = c.pieces;
-  j.tile_bin = (u32*)(base + c.off_tiles);
-  j.cap_tiles = c.tiles;
   st->c = c;
   st->dev = dev;
-  int sms = sm_count(dev);
-  if (p.sm_limit && (int)p.sm_limit < sms) sms = (int)p.sm_limit;
   st->sms = sms;
   return RS_OK;
 }
@@ -281,14 +281,13 @@ static int timed(u32 kernel, u32 level, cudaStream_t s, F&& launch) {
 // Levels 0..K-1 of distribution passes, then the on-chip sorts and the copy-back.
 static rs_status run_levels(const Setup& st, cudaStream_t s) {
   const Job& j = st.j;
-  const u32 gh = (u32)st.sms * (u32)hist_ctas_per_sm(j);
-  const u32 gs = (u32)st.sms * (u32)scatter_ctas_per_sm(j, j.wide != 0);
+  const u32 gs = (u32)st.sms * (u32)scatter_ctas_per_sm(j);
   const u32 gc = (u32)st.sms * 2;
   const int levels = (int)j.K;  // each level consumes >= 8 key bits
   for (int lv = 0; lv < levels; lv++) {
-    if (timed(RS_K_HIST, lv, s, [&] { return launch_hist(j, lv, 0, gh, s); }) < 0) return RS_ERR_CUDA;
-    if (timed(RS_K_HIST_REDO, lv, s, [&] { return launch_hist(j, lv, 1, gh, s); }) < 0) return RS_ERR_CUDA;
-    if (timed(RS_K_SCATTER, lv, s, [&] { return launch_scatter(j, lv, j.wide != 0, gs, s); }) < 0) return RS_ERR_CUDA;
+    if (timed(RS_K_HIST, lv, s, [&] { return launch_hist(j, lv, 0, s); }) < 0) return RS_ERR_CUDA;
+    if (timed(RS_K_HIST_REDO, lv, s, [&] { return launch_hist(j, lv, 1, s); }) < 0) return RS_ERR_CUDA;
+    if (timed(RS_K_SCATTER, lv, s, [&] { return launch_scatter(j, lv, gs, s); }) < 0) return RS_ERR_CUDA;
     if (timed(RS_K_CLASSIFY, lv, s, [&] { return launch_classify(j, lv, gc, s); }) < 0) return RS_ERR_CUDA;
   }
   const u32 gch = (u32)st.sms * (u32)chunk_ctas_per_sm(j);
@@ -347,9 +346,7 @@ static rs_status noalloc_setup(void* in, void* tmp, u64 n, u32 rec_size, u32 key
   j.wmax = sh.wmax;
   j.T = sh.T;
   j.chunk_max = sh.chunk_max;
-  j.watchdog = p.watchdog_polls ? p.watchdog_polls : (1u << 16);
-  j.wide = sh.wide ? 1u : 0u;
-  const Caps c = caps_for(n, j.T, j.chunk_max, j.wmax, j.wide != 0, 0);
+  const Caps c = caps_for(n, j.chunk_max, j.wmax, 0);
   if (c.bytes > kNoAllocBytes) return RS_ERR_TOO_LARGE;
   st->c = c;
   return RS_OK;
@@ -365,29 +362,26 @@ static void noalloc_carve(Setup* st, char* base) {
   j.base[0] = (u64*)(base + c.off_base0);
   j.base[1] = (u64*)(base + c.off_base1);
   j.cap_base = c.base;
-  j.status[0] = j.status[1] = base + c.off_status;
-  j.cap_status = c.status;
+  j.seg = (u64*)(base + c.off_seg);
+  j.cap_seg = c.seg;
   j.chunks = (Chunk*)(base + c.off_chunks);
   j.cap_chunks = c.chunks;
   j.pieces = (Piece*)(base + c.off_pieces);
   j.cap_pieces = c.pieces;
-  j.tile_bin = (u32*)(base + c.off_tiles);
-  j.cap_tiles = c.tiles;
 }
 
 // The level sequence of run_levels, launched without the optional timing events.
 static rs_status noalloc_levels(const Setup& st, cudaStream_t s) {
   const Job& j = st.j;
-  const u32 gh = (u32)st.sms * (u32)hist_ctas_per_sm(j);
-  const u32 gs = (u32)st.sms * (u32)scatter_ctas_per_sm(j, j.wide != 0);
+  const u32 gs = (u32)st.sms * (u32)scatter_ctas_per_sm(j);
   const u32 gc = (u32)st.sms * 2;
   int k;
   for (int lv = 0; lv < (int)j.K; lv++) {
-    if ((k = launch_hist(j, lv, 0, gh, s)) < 0) return RS_ERR_CUDA;
+    if ((k = launch_hist(j, lv, 0, s)) < 0) return RS_ERR_CUDA;
     count(k);
-    if ((k = launch_hist(j, lv, 1, gh, s)) < 0) return RS_ERR_CUDA;
+    if ((k = launch_hist(j, lv, 1, s)) < 0) return RS_ERR_CUDA;
     count(k);
-    if ((k = launch_scatter(j, lv, j.wide != 0, gs, s)) < 0) return RS_ERR_CUDA;
+    if ((k = launch_scatter(j, lv, gs, s)) < 0) return RS_ERR_CUDA;
     count(k);
     if ((k = launch_classify(j, lv, gc, s)) < 0) return RS_ERR_CUDA;
     count(k);
@@ -471,20 +465,19 @@ static rs_status one_pass(const void* src, void* dst, uint64_t n, uint32_t rec_s
     return r;
   Job& j = st.j;
   j.wmax = kWMax;  // the requested width, whatever the plan says
-  const u32 gh = (u32)st.sms * (u32)hist_ctas_per_sm(j);
   int k;
   if ((k = launch_init_plain(j, bit_lo, width, s)) < 0) return RS_ERR_CUDA;
   count(k);
   if (counts) {
-    if ((k = launch_hist(j, 0, 2, gh, s)) < 0) return RS_ERR_CUDA;
+    if ((k = launch_hist(j, 0, 2, s)) < 0) return RS_ERR_CUDA;
     count(k);
     if ((k = launch_read_counts(j, (u64*)counts, width, s)) < 0) return RS_ERR_CUDA;
     count(k);
     return RS_OK;
   }
-  if ((k = launch_hist(j, 0, 3, gh, s)) < 0) return RS_ERR_CUDA;
+  if ((k = launch_hist(j, 0, 3, s)) < 0) return RS_ERR_CUDA;
   count(k);
-  if ((k = launch_scatter(j, 0, j.wide != 0, (u32)st.sms * (u32)scatter_ctas_per_sm(j, j.wide != 0), s)) < 0)
+  if ((k = launch_scatter(j, 0, (u32)st.sms * (u32)scatter_ctas_per_sm(j), s)) < 0)
     return RS_ERR_CUDA;
   count(k);
   return RS_OK;
@@ -591,7 +584,7 @@ uint32_t radix_sort_chunk_records(uint32_t rec_size) {
 uint64_t radix_sort_workspace_bytes(uint64_t n, uint32_t rec_size, uint32_t key_size, uint64_t n_segs) {
   if (validate_layout(rec_size, key_size) != RS_OK || n > UINT64_MAX / rec_size) return 0;
   const Shape sh = shape_for(n, rec_size, key_size, current_plan());
-  return (uint64_t)caps_for(n, sh.T, sh.chunk_max, sh.wmax, sh.wide, n_segs).bytes;
+  return (uint64_t)caps_for(n, sh.chunk_max, sh.wmax, n_segs).bytes;
 }
 
 rs_status radix_sort_reserve(uint64_t n, uint32_t rec_size, uint32_t key_size, uint64_t n_segs, rs_stream_t stream) {
@@ -601,7 +594,7 @@ rs_status radix_sort_reserve(uint64_t n, uint32_t rec_size, uint32_t key_size, u
   int dev = 0;
   if (cudaGetDevice(&dev) != cudaSuccess) return RS_ERR_CUDA;
   const Shape sh = shape_for(n, rec_size, key_size, current_plan());
-  const Caps c = caps_for(n, sh.T, sh.chunk_max, sh.wmax, sh.wide, n_segs);
+  const Caps c = caps_for(n, sh.chunk_max, sh.wmax, n_segs);
   Workspace* w = nullptr;
   return get_workspace(dev, (cudaStream_t)stream, c.bytes, &w);
 }
@@ -664,6 +657,7 @@ rs_status radix_sort_noalloc(void* in, void* tmp, uint64_t n, uint32_t rec_size,
   if (p.sm_limit && (int)p.sm_limit < sms) sms = (int)p.sm_limit;
   st.sms = sms;
   st.dev = dev;
+  st.j.lanes = lanes_for(st.j, sms);
   const Job& j = st.j;
   // the array keeps the previous call's contents: its error word starts this call at zero,
   // and the init kernels rewrite the rest of the control block and the first bin list

@@ -120,7 +120,9 @@ struct DigitSpec {
   template <int KW>
   __device__ __forceinline__ u32 of(const Key<KW>& k) const {
     u32 d = digit_of<KW>(k, lo, w);
-    if (sb) d |= (digit_of<KW>(k, plo, pw) - v0) << w;
+    // (masked: a record whose parent digit lies outside the chunk's sub-bins -- possible
+    // only after a reported error -- must still index inside the counters)
+    if (sb) d |= ((digit_of<KW>(k, plo, pw) - v0) & ((1u << sb) - 1)) << w;
     return d;
   }
 };

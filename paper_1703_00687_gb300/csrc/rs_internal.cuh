@@ -43,7 +43,6 @@ struct Bin {
   u64 size;         // records
   u64 tile_start;   // number of the bin's first tile within its level
   u64 base_off;     // first of its 2^W entries in the level's bucket-base pool
-  u64 status_off;   // first of its tiles * 2^W look-back words
   u64 kand[2];      // AND / OR of the bin's keys, gathered by the histogram pass: they tell
   u64 kor[2];       // whether the digit starts at the highest differing bit, or all keys are equal
   u32 lo, W;        // the digit is key bits [lo, lo + W)
@@ -82,14 +81,10 @@ struct Ctl {
   u64 nbins[2];
   u64 ntiles[2];
   u64 base_used[2];
-  u64 status_used[2];
-  u64 s_ticket;     // tile dispenser of the scatter pass
   u32 cls_done;     // classify CTAs finished (the last one finalises the next list)
   u32 nredo;        // bins of this level whose digit moved after the count (recount needed)
   u64 nchunks, chunk_ticket;
   u64 npieces, piece_ticket;
-  u32 never;        // stays 0: the word an injected stall waits on
-  u32 pad2;
 };
 
 // Everything a kernel needs about one call, passed by value.
@@ -102,20 +97,17 @@ struct Job {
   u32 T;              // records per tile of a distribution pass
   u32 chunk_max;      // largest range one CTA sorts on chip
   u32 wmax;           // widest digit of a pass (<= kWMax)
-  u32 watchdog;       // look-back polls before giving up
-  u32 wide;           // look-back words are 64-bit (bins of 2^30 records or more)
-  u32 inject;         // testing: 1 = the first look-back wait of a pass waits on Ctl::never
-  u32 pad;
+  u32 lanes;          // tile ranges of a distribution level (one per histogram CTA)
+  u32 inject;         // testing: 1 = the first scatter pass finds one digit run out of range
+
   u64 keymask[2];     // key bits of words 0 and 1
   Ctl* ctl;
   Bin* bins[2];
   u64 cap_bins;
   u64* base[2];       // bucket counts, then (after the scan) bucket bases
   u64 cap_base;
-  void* status[2];    // look-back words (u32 or u64)
-  u64 cap_status;
-  u32* tile_bin;      // bin of every tile of the current level (written by the histogram pass)
-  u64 cap_tiles;
+  u64* seg;           // per (lane, bin) segment and digit: counts, then run starts (2^wmax each)
+  u64 cap_seg;        // segments
   Chunk* chunks;
   u64 cap_chunks;
   Piece* pieces;
@@ -125,6 +117,12 @@ struct Job {
 };
 
 constexpr u64 kPieceRecords = 1ull << 16;      // copy-back granularity
+constexpr u32 kMaxLanes = 1024;                // tile ranges per level, at most
+
+// Lane of tile t: level tiles are split into j.lanes contiguous ranges of `per` tiles.  The
+// part of bin b inside lane c is segment c + b (unique: a later lane never reaches back to an
+// earlier bin), so a level needs at most lanes + bins segments.
+__host__ __device__ inline u64 lane_tiles(u64 ntiles, u32 lanes) { return (ntiles + lanes - 1) / lanes; }
 
 // ---------------------------------------------------------------------------- keys
 template <int KW>
@@ -403,8 +401,8 @@ __device__ __forceinline__ void store_words(u64* dst, const u64* src, u64 words)
 int launch_init_plain(const Job& j, u32 lo, u32 W, cudaStream_t s);
 int launch_init_single_chunk(const Job& j, cudaStream_t s);
 int launch_init_segments(const Job& j, u32 grid, cudaStream_t s);
-int launch_hist(const Job& j, int level, int mode, u32 grid, cudaStream_t s);
-int launch_scatter(const Job& j, int level, bool wide_status, u32 grid, cudaStream_t s);
+int launch_hist(const Job& j, int level, int mode, cudaStream_t s);  // grid = j.lanes
+int launch_scatter(const Job& j, int level, u32 grid, cudaStream_t s);
 int launch_classify(const Job& j, int level, u32 grid, cudaStream_t s);
 int launch_chunks(const Job& j, u32 grid, cudaStream_t s);
 int launch_copy(const Job& j, u32 grid, cudaStream_t s);
@@ -413,7 +411,7 @@ int launch_read_counts(const Job& j, u64* d_counts, u32 W, cudaStream_t s);
 // smem bytes and CTAs per SM of the tile/chunk kernels for a job
 size_t scatter_smem_bytes(const Job& j);
 size_t chunk_smem_bytes(const Job& j);
-int scatter_ctas_per_sm(const Job& j, bool wide_status);
+int scatter_ctas_per_sm(const Job& j);
 int chunk_ctas_per_sm(const Job& j);
 int hist_ctas_per_sm(const Job& j);
 

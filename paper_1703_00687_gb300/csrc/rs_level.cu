@@ -78,7 +78,6 @@ __global__ void __launch_bounds__(kThreads) k_init_plain(Job j, u32 lo, u32 W) {
     c.nbins[0] = 1;
     c.ntiles[0] = tiles;
     c.base_used[0] = nd;
-    c.status_used[0] = tiles * nd;
     *ctl = c;
     Bin b = {};
     b.begin = 0;
@@ -138,8 +137,7 @@ __global__ void __launch_bounds__(kThreads) k_init_segments(Job j) {
     const u64 tiles = ceil_div(c, j.T);
     const u64 idx = atomicAdd(&ctl->nbins[0], 1ull);
     const u64 bo = atomicAdd(&ctl->base_used[0], (u64)nd);
-    const u64 so = atomicAdd(&ctl->status_used[0], tiles * nd);
-    if (idx >= j.cap_bins || bo + nd > j.cap_base || so + tiles * nd > j.cap_status) {
+    if (idx >= j.cap_bins || bo + nd > j.cap_base) {
       atomicOr(&ctl->err, kErrOverflow);
       continue;
     }
@@ -147,7 +145,6 @@ __global__ void __launch_bounds__(kThreads) k_init_segments(Job j) {
     b.begin = a;
     b.size = c;
     b.base_off = bo;
-    b.status_off = so;
     b.kand[0] = b.kand[1] = ~0ull;
     b.lo = lo;
     b.W = W;
@@ -219,6 +216,30 @@ __device__ void finish_bin(const Job& j, int L, u64 b, int mode) {
   if (v0 < nd) base[v0] = ex;
   if (v0 + 1 < nd) base[v0 + 1] = ex + c0;
   if (mode == 1 && threadIdx.x == 0) bp->flags &= ~kBinRedo;
+  // Run starts of the scatter: the part of the bin inside lane c writes digit v from
+  // bucket base + (records of digit v in the bin's earlier lanes).  Every lane that holds
+  // tiles of the bin has stored its counts in its segment before the bin was finished.
+  const u64 per = lane_tiles(j.ctl->ntiles[L], j.lanes);
+  const u64 ts = bp->tile_start, nt = ceil_div(size, (u64)j.T);
+  const u64 cfirst = ts / per, clast = (ts + nt - 1) / per;
+  if (clast + b >= j.cap_seg) {  // cannot happen: lanes + bins segments are allocated
+    if (threadIdx.x == 0) atomicOr(&j.ctl->err, kErrOverflow);
+    return;
+  }
+  u64 r0 = ex, r1 = ex + c0;
+  for (u64 c = cfirst; c <= clast; c++) {
+    u64* sg = j.seg + ((c + b) << j.wmax);
+    if (v0 < nd) {
+      const u64 t = __ldcg(sg + v0);
+      sg[v0] = r0;
+      r0 += t;
+    }
+    if (v0 + 1 < nd) {
+      const u64 t = __ldcg(sg + v0 + 1);
+      sg[v0 + 1] = r1;
+      r1 += t;
+    }
+  }
 }
 
 // Shared memory of k_hist: two buffers of a tile's keys (tile t+1 streams in while tile t
@@ -243,8 +264,9 @@ __global__ void __launch_bounds__(kThreads, 2) k_hist(Job j, int level, int mode
   const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
   const bool want_masks = mode == 0;
   const u32 T = j.T;
-  const u64 per = ceil_div(ntiles, gridDim.x);
-  const u64 t0 = blockIdx.x * per;
+  const u64 per = lane_tiles(ntiles, j.lanes);  // one CTA per lane
+  const u64 lane_id = blockIdx.x;
+  const u64 t0 = lane_id * per;
   const u64 t1 = min(ntiles, t0 + per);
   if (t0 >= t1) return;
   for (u32 v = tid; v < (kHistCopies << kWMax); v += kThreads) hist[v] = 0;
@@ -258,6 +280,12 @@ __global__ void __launch_bounds__(kThreads, 2) k_hist(Job j, int level, int mode
     const Bin* bb = &bins[b];
     const u32 nd = 1u << bb->W;
     const u64 bo = bb->base_off;
+    const u64 sid = lane_id + b;  // segment of (lane, bin)
+    if (sid >= j.cap_seg) {    // cannot happen: lanes + bins segments are allocated
+      if (tid == 0) atomicOr(&ctl->err, kErrOverflow);
+      return;
+    }
+    u64* sg = j.seg + (sid << j.wmax);
     for (u32 v = tid; v < nd; v += kThreads) {
       u32 h = 0;
 #pragma unroll
@@ -266,6 +294,7 @@ __global__ void __launch_bounds__(kThreads, 2) k_hist(Job j, int level, int mode
         hist[(c << kWMax) + v] = 0;
       }
       if (h) atomicAdd(&j.base[L][bo + v], (u64)h);
+      if (mode != 2) sg[v] = h;  // this lane's part of the bin (the scatter's run starts)
     }
     if (want_masks) {
 #pragma unroll
@@ -314,7 +343,7 @@ __global__ void __launch_bounds__(kThreads, 2) k_hist(Job j, int level, int mode
     u32 cnt, lo, W, skip;
   };
   u64 walk = find_bin(bins, nb, t0);
-  // locate tile t, clear its look-back words, and start copying its keys into buffer `buf`
+  // locate tile t and start copying its keys into buffer `buf`
   auto issue = [&](u64 t, int buf) {
     while (walk + 1 < nb && bins[walk + 1].tile_start <= t) walk++;
     const Bin* bp = &bins[walk];
@@ -326,18 +355,6 @@ __global__ void __launch_bounds__(kThreads, 2) k_hist(Job j, int level, int mode
     const u64 tib = t - bp->tile_start;
     const u64 r0 = tib * T;
     tr.cnt = (u32)min((u64)T, bp->size - r0);
-    if ((mode == 0 || mode == 3) && tid == 0 && t < j.cap_tiles) j.tile_bin[t] = (u32)walk;
-    if (mode == 0 || mode == 3) {  // the scatter pass's look-back words of this tile start cleared
-      const u32 nd = 1u << tr.W;
-      const u64 so = bp->status_off + tib * nd;
-      if (j.wide) {
-        u64* st = (u64*)j.status[L] + so;
-        for (u32 v = tid; v < nd; v += kThreads) st[v] = 0;
-      } else {
-        u32* st = (u32*)j.status[L] + so;
-        for (u32 v = tid; v < nd; v += kThreads) st[v] = 0;
-      }
-    }
     if (!tr.skip) {
       const u64* src = j.buf[bp->parity] + (bp->begin + r0) * j.RW;
       u64* dst = kbuf + (size_t)buf * T * KW;
@@ -415,83 +432,6 @@ __host__ __device__ inline ScatterLayout scatter_layout(u32 T, u32 RW, u32 wmax)
   return s;
 }
 
-// Look-back word: 2-bit state (0 none, 1 tile count, 2 inclusive prefix) above the value.
-template <typename S>
-struct LB;
-template <>
-struct LB<u32> {
-  static constexpr int kShift = 30;
-  static constexpr u32 kVal = (1u << 30) - 1;
-};
-template <>
-struct LB<u64> {
-  static constexpr int kShift = 62;
-  static constexpr u64 kVal = (1ull << 62) - 1;
-};
-
-// Publishes this tile's count of one digit and returns the number of records with that digit
-// in the bin's earlier tiles (decoupled look-back).  A look-back word carries its state and its
-// count together, so plain relaxed accesses suffice (no fences).  The words of up to
-// LookAhead<S>::n earlier tiles are read together, one round trip per group.  Every wait is bounded.
-template <typename S>
-struct LookAhead {  // predecessors read per round trip (fewer for the rare 64-bit words: registers)
-  static constexpr int n = sizeof(S) == 4 ? 8 : 3;
-};
-
-template <typename S>
-__device__ __forceinline__ void lb_publish(S* st, u64 self, u64 tib, u32 c) {
-  st_relaxed(st + self, (S)(((S)(tib == 0 ? 2 : 1) << LB<S>::kShift) | (S)c));
-}
-
-template <typename S>
-__device__ __forceinline__ S lb_word(const S* st, u64 at, bool stall, Ctl* ctl) {
-  return stall ? (S)ld_relaxed(&ctl->never) : ld_relaxed(st + at);
-}
-
-// Reads the words of the LookAhead<S>::n tiles before this one (one round trip).
-template <typename S>
-__device__ __forceinline__ void lb_first(const S* st, u64 self, u32 nd, u64 tib, bool stall, Ctl* ctl, S (&w)[LookAhead<S>::n]) {
-#pragma unroll
-  for (int q = 0; q < LookAhead<S>::n; q++)
-    if ((u64)q < tib) w[q] = lb_word(st, self - (u64)(q + 1) * nd, stall && q == 0, ctl);
-}
-
-// Walks back from the words lb_first read, waiting (bounded) for tiles not yet published and
-// reading further groups while only aggregates are found; then publishes the inclusive prefix.
-template <typename S>
-__device__ __forceinline__ u64 lb_collect(S* st, u64 self, u32 nd, u64 tib, u32 c, const Job& j, bool stall, S (&w)[LookAhead<S>::n]) {
-  Ctl* ctl = j.ctl;
-  if (tib == 0) return 0;
-  u64 excl = 0;
-  u64 back = 1;  // distance of w[0]
-  bool done = false;
-  for (;;) {
-    const u64 n = min((u64)LookAhead<S>::n, tib - back + 1);
-#pragma unroll
-    for (int q = 0; q < LookAhead<S>::n && !done; q++) {
-      if ((u64)q >= n) break;
-      u32 polls = 0;
-      while ((w[q] >> LB<S>::kShift) == 0) {  // a tile not yet published
-        if (++polls > j.watchdog || ((polls & 255) == 0 && (*(volatile u32*)&ctl->err & kErrTimeout))) {
-          atomicOr(&ctl->err, kErrTimeout);
-          break;
-        }
-        __nanosleep(100);
-        w[q] = lb_word(st, self - (back + q) * nd, stall && back + q == 1, ctl);
-      }
-      excl += (u64)(w[q] & LB<S>::kVal);
-      if ((w[q] >> LB<S>::kShift) != 1) done = true;  // inclusive prefix (or gave up)
-    }
-    back += n;
-    if (done || back > tib) break;
-#pragma unroll
-    for (int q = 0; q < LookAhead<S>::n; q++)
-      if ((u64)q < tib - back + 1) w[q] = ld_relaxed(st + self - (back + q) * nd);
-  }
-  st_relaxed(st + self, (S)(((S)2 << LB<S>::kShift) | (S)(excl + c)));
-  return excl;
-}
-
 // Lanes of the warp whose digit equals this lane's (d has W significant bits): one vote per
 // digit bit.  Lanes with valid == false get a mask of their own.
 __device__ __forceinline__ u32 peers_of(u32 d, u32 W, bool valid) {
@@ -515,44 +455,21 @@ __device__ __forceinline__ u32 staged_digit(const u64* rec, u32 lo, u32 W) {
 
 constexpr u64 kSkip = ~0ull;  // gbase of a digit whose run would leave its bin
 
-// Turns the tile's digit counts into destinations: the exclusive scan over digits (tbase) and,
-// per digit, the records of that digit in the bin's earlier tiles (decoupled look-back).  The
-// first look-back words of all of a thread's digits are read together (one round trip).  A
-// digit run that would leave the bin (possible only after a failed wait or a corrupted
-// histogram) gets kSkip and is not written.
-template <typename S, u32 Q>
-__device__ __forceinline__ void tile_offsets(S* st, u64 status_off, u64 tib, u32 nd, const u32* tcount, u32* tbase,
-                                             u32* scan_scr, const u64 (&mybase)[Q], u64 begin, u64 size, const Job& j,
-                                             u64* gbase) {
-  const u32 tid = threadIdx.x;
-  block_exclusive_scan<kSThreads>(tbase, nd, scan_scr);
-  S w[Q][LookAhead<S>::n];
-#pragma unroll
-  for (u32 q = 0; q < Q; q++) {
-    const u32 v = tid + q * kSThreads;
-    if (v < nd) lb_first<S>(st, status_off + tib * nd + v, nd, tib, j.inject && v == 0 && tib == 1, j.ctl, w[q]);
-  }
-#pragma unroll
-  for (u32 q = 0; q < Q; q++) {
-    const u32 v = tid + q * kSThreads;
-    if (v >= nd) break;
-    const u32 c = tcount[v];
-    const u64 excl = lb_collect<S>(st, status_off + tib * nd + v, nd, tib, c, j, j.inject && v == 0 && tib == 1, w[q]);
-    const u64 first = mybase[q] + excl;  // the run's first record, relative to the bin
-    u64 g = begin + first - tbase[v];
-    if (c && (first > size || c > size - first)) {
-      atomicOr(&j.ctl->err, kErrInternal);
-      g = kSkip;
-    }
-    gbase[v] = g;
-  }
-}
-
-// IT = records per thread (T = kSThreads * IT).  Tiles are taken one at a time from a ticket
-// dispenser, in order, so that every tile a look-back waits for is already held by a running
-// CTA that will publish its counts without waiting for anything later.
+// Stable scatter of every large bin of the level into the other buffer.  The level's tiles
+// are split into the same lanes as in the histogram pass (contiguous tile ranges); a CTA
+// takes its lanes in turn and walks each lane's tiles in order.  The histogram pass left,
+// for every (lane, bin) segment and digit, where the segment's records of that digit start
+// (bucket base + the digit's records in the bin's earlier lanes), so a tile's destinations
+// are known from those starts plus the digit counts of the lane's earlier tiles of the bin,
+// which the CTA keeps in registers: no tile waits for another.
+//
+// Per tile of T = kSThreads * IT records: the records are staged in shared memory; warp w
+// ranks its strip of records in order (peer masks by one vote per digit bit, per-warp 16-bit
+// counters), so the order inside a digit is the input order (stable); the digit counts are
+// scanned; then the tile is written in digit order, so consecutive threads write consecutive
+// records of a run with 16-byte streaming stores.
 template <int KW, int RWT, int IT>
-__global__ void __launch_bounds__(kSThreads) k_scatter(Job j, int level) {
+__global__ void __launch_bounds__(kSThreads, 2) k_scatter(Job j, int level) {
   const int L = level & 1;
   Ctl* ctl = j.ctl;
   const u64 nb = ctl->nbins[L];
@@ -573,8 +490,6 @@ __global__ void __launch_bounds__(kSThreads) k_scatter(Job j, int level) {
   u32* tcount = (u32*)(smem + lay.tcount);
   u32* tbase = (u32*)(smem + lay.tbase);
   u64* gbase = (u64*)(smem + lay.gbase);
-  __shared__ u64 s_ticket;
-  __shared__ u32 s_bin;
   __shared__ u32 scan_scr[kSWarps + 1];
   const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
   const u32 ltmask = lanemask_lt();
@@ -582,137 +497,157 @@ __global__ void __launch_bounds__(kSThreads) k_scatter(Job j, int level) {
   // run; they are zeroed again while the tile is written out
   for (u32 i = tid; i < kSWarps * WS; i += kSThreads) whist[i] = 0;
   u16* wh = whist + warp * WS;
-  for (;;) {
-    if (tid == 0) {
-      const u64 tk = atomicAdd(&ctl->s_ticket, 1ull);
-      s_ticket = tk;
-      s_bin = tk < ntiles && tk < j.cap_tiles ? j.tile_bin[tk] : 0;
-    }
-    __syncthreads();
-    const u64 t = s_ticket;
-    const u32 b = s_bin;
-    __syncthreads();  // every thread has its ticket before thread 0 may take the next
-    if (t >= ntiles) break;
-    const Bin* bp = &bins[b < nb ? b : 0];
-    const u32 lo = bp->lo, W = bp->W, nd = 1u << W;
-    const u64 begin = bp->begin, size = bp->size;
-    const u64 tib = t - bp->tile_start;
-    const u64 status_off = bp->status_off;
-    const u32 parity = bp->parity;
-    if ((bp->flags & kBinEqual) || tib * T >= size) continue;  // finished bin (or inconsistent map)
-    const u64 r0 = tib * T;
-    const u32 cnt = (u32)min((u64)T, size - r0);
-    u64* dstb = j.buf[parity ^ 1];
-    const u64* bbase = j.base[L] + bp->base_off;
+  const u64 per = lane_tiles(ntiles, j.lanes);
+  bool inject = j.inject != 0 && blockIdx.x == 0 && tid == 0;  // testing: fail one run check
+  __syncthreads();
 
-    load_words_async<kSThreads>(stage, j.buf[parity] + (begin + r0) * RW, (u64)cnt * RW);
-    u64 mybase[kDigitsPerThread];  // this thread's digits' bucket bases, fetched during the load
-#pragma unroll
-    for (u32 q = 0; q < kDigitsPerThread; q++) {
-      const u32 v = tid + q * kSThreads;
-      mybase[q] = v < nd ? bbase[v] : 0;
-    }
-    cp_async_wait_all();
-    __syncthreads();
+  for (u64 ln = blockIdx.x; ln < j.lanes; ln += gridDim.x) {
+    const u64 t0 = ln * per, t1 = min(ntiles, t0 + per);
+    if (t0 >= t1) break;  // later lanes are empty too
+    u64 b = find_bin(bins, nb, t0);
+    u64 cur = ~0ull;
+    u64 run[kDigitsPerThread];    // this thread's digits: start of the next run, bin-relative
+    for (u64 t = t0; t < t1; t++) {
+      while (b + 1 < nb && bins[b + 1].tile_start <= t) b++;
+      const Bin* bp = &bins[b];
+      const u32 lo = bp->lo, W = bp->W, nd = 1u << W;
+      const u64 begin = bp->begin, size = bp->size;
+      const u64 tib = t - bp->tile_start;
+      const u32 parity = bp->parity;
+      if ((bp->flags & kBinEqual) || tib * T >= size) continue;  // finished bin (or inconsistent list)
+      const u64 r0 = tib * T;
+      const u32 cnt = (u32)min((u64)T, size - r0);
+      u64* dstb = j.buf[parity ^ 1];
 
-    // stable rank: warp w owns records [w*PW, (w+1)*PW), visited in order
-    u32 packed[IT];
-    if (cnt == T) {
-      // first every item's digit and peers (independent of each other), then the counters
-      u32 dg[IT], pr[IT];
+      load_words_async<kSThreads>(stage, j.buf[parity] + (begin + r0) * RW, (u64)cnt * RW);
+      if (b != cur) {  // first tile of this lane's part of the bin: its run starts
+        cur = b;
+        const u64* sg = j.seg + ((ln + b) << j.wmax);
 #pragma unroll
-      for (int it = 0; it < IT; it++) {
-        dg[it] = staged_digit<KW>(stage + (u64)(warp * PW + it * 32 + lane) * RW, lo, W);
-        pr[it] = peers_of(dg[it], W, true);
+        for (u32 q = 0; q < kDigitsPerThread; q++) {
+          const u32 v = tid + q * kSThreads;
+          run[q] = v < nd ? sg[v] : 0;
+        }
       }
+      cp_async_wait_all();
+      __syncthreads();
+
+      // stable rank: warp w owns records [w*PW, (w+1)*PW), visited in order
+      u32 packed[IT];
+      if (cnt == T) {
+        // first every item's digit and peers (independent of each other), then the counters
+        u32 dg[IT], pr[IT];
 #pragma unroll
-      for (int it = 0; it < IT; it++) {
-        const u32 d = dg[it], peers = pr[it];
-        const u32 before = __popc(peers & ltmask);
-        const u32 old = wh[d];
-        __syncwarp();
-        if (before == 0) wh[d] = (u16)(old + __popc(peers));
-        __syncwarp();
-        packed[it] = (old + before) | (d << 16);
+        for (int it = 0; it < IT; it++) {
+          dg[it] = staged_digit<KW>(stage + (u64)(warp * PW + it * 32 + lane) * RW, lo, W);
+          pr[it] = peers_of(dg[it], W, true);
+        }
+#pragma unroll
+        for (int it = 0; it < IT; it++) {
+          const u32 d = dg[it], peers = pr[it];
+          const u32 before = __popc(peers & ltmask);
+          const u32 old = wh[d];
+          __syncwarp();
+          if (before == 0) wh[d] = (u16)(old + __popc(peers));
+          __syncwarp();
+          packed[it] = (old + before) | (d << 16);
+        }
+      } else {
+#pragma unroll
+        for (int it = 0; it < IT; it++) {
+          const u32 r = warp * PW + it * 32 + lane;
+          const bool valid = r < cnt;
+          u32 d = 0;
+          if (valid) d = staged_digit<KW>(stage + (u64)r * RW, lo, W);
+          const u32 peers = peers_of(d, W, valid);
+          const u32 before = __popc(peers & ltmask);
+          u32 old = 0;
+          if (valid) old = wh[d];
+          __syncwarp();
+          if (valid && before == 0) wh[d] = (u16)(old + __popc(peers));
+          __syncwarp();
+          packed[it] = valid ? ((old + before) | (d << 16)) : 0xffffffffu;
+        }
       }
-    } else {
+      __syncthreads();
+      for (u32 v = tid; v < nd; v += kSThreads) {
+        u32 acc = 0;
 #pragma unroll
-      for (int it = 0; it < IT; it++) {
-        const u32 r = warp * PW + it * 32 + lane;
-        const bool valid = r < cnt;
-        u32 d = 0;
-        if (valid) d = staged_digit<KW>(stage + (u64)r * RW, lo, W);
-        const u32 peers = peers_of(d, W, valid);
-        const u32 before = __popc(peers & ltmask);
-        u32 old = 0;
-        if (valid) old = wh[d];
-        __syncwarp();
-        if (valid && before == 0) wh[d] = (u16)(old + __popc(peers));
-        __syncwarp();
-        packed[it] = valid ? ((old + before) | (d << 16)) : 0xffffffffu;
+        for (int w = 0; w < kSWarps; w++) {
+          const u32 x = whist[w * WS + v];
+          whist[w * WS + v] = (u16)acc;
+          acc += x;
+        }
+        tcount[v] = acc;
+        tbase[v] = acc;
       }
-    }
-    __syncthreads();
-    for (u32 v = tid; v < nd; v += kSThreads) {
-      u32 run = 0;
+      __syncthreads();
+      block_exclusive_scan<kSThreads>(tbase, nd, scan_scr);
+      // destinations of this tile's runs; a run that would leave its bin (possible only with
+      // corrupted counts) is reported and not written
 #pragma unroll
-      for (int w = 0; w < kSWarps; w++) {
-        const u32 x = whist[w * WS + v];
-        whist[w * WS + v] = (u16)run;
-        run += x;
+      for (u32 q = 0; q < kDigitsPerThread; q++) {
+        const u32 v = tid + q * kSThreads;
+        if (v >= nd) break;
+        const u32 c = tcount[v];
+        const u64 first = run[q];
+        run[q] += c;
+        u64 g = begin + first - tbase[v];
+        bool bad = c && (first > size || c > size - first);
+        if (c && inject) {
+          bad = true;
+          inject = false;
+        }
+        if (bad) {
+          atomicOr(&ctl->err, kErrInternal);
+          g = kSkip;
+        }
+        gbase[v] = g;
       }
-      tcount[v] = run;
-      tbase[v] = run;
-      // publish this tile's count at once: later tiles of the bin may be waiting for it
-      if (j.wide) lb_publish<u64>((u64*)j.status[L], status_off + tib * nd + v, tib, run);
-      else lb_publish<u32>((u32*)j.status[L], status_off + tib * nd + v, tib, run);
-    }
-    __syncthreads();
-    if (j.wide) tile_offsets<u64, kDigitsPerThread>((u64*)j.status[L], status_off, tib, nd, tcount, tbase, scan_scr, mybase, begin, size, j, gbase);
-    else tile_offsets<u32, kDigitsPerThread>((u32*)j.status[L], status_off, tib, nd, tcount, tbase, scan_scr, mybase, begin, size, j, gbase);
-    if (cnt == T) {
+      if (cnt == T) {
 #pragma unroll
-      for (int it = 0; it < IT; it++) {
-        const u32 d = packed[it] >> 16;
-        const u32 slot = tbase[d] + wh[d] + (packed[it] & 0xffffu);
-        perm[slot] = (u16)(warp * PW + it * 32 + lane);
-        sdig[slot] = (u16)d;
-      }
-    } else {
-#pragma unroll
-      for (int it = 0; it < IT; it++) {
-        if (packed[it] != 0xffffffffu) {
+        for (int it = 0; it < IT; it++) {
           const u32 d = packed[it] >> 16;
           const u32 slot = tbase[d] + wh[d] + (packed[it] & 0xffffu);
           perm[slot] = (u16)(warp * PW + it * 32 + lane);
           sdig[slot] = (u16)d;
         }
-      }
-    }
-    __syncthreads();
-    // per-warp counters back to zero for the next tile (nothing reads them before then)
-    for (u32 v = tid; v < nd; v += kSThreads) {
+      } else {
 #pragma unroll
-      for (int w = 0; w < kSWarps; w++) whist[w * WS + v] = 0;
-    }
-    // write the tile in digit order: consecutive slots of one digit go to consecutive records
-    if (RW == 2) {
-      for (u32 s = tid; s < cnt; s += kSThreads) {
-        const u64 g = gbase[sdig[s]];
-        if (g == kSkip) continue;
-        const ulonglong2 v = *reinterpret_cast<const ulonglong2*>(stage + 2 * (u32)perm[s]);
-        __stcs(reinterpret_cast<ulonglong2*>(dstb + 2 * (g + s)), v);
+        for (int it = 0; it < IT; it++) {
+          if (packed[it] != 0xffffffffu) {
+            const u32 d = packed[it] >> 16;
+            const u32 slot = tbase[d] + wh[d] + (packed[it] & 0xffffu);
+            perm[slot] = (u16)(warp * PW + it * 32 + lane);
+            sdig[slot] = (u16)d;
+          }
+        }
       }
-    } else {
-      for (u32 s = tid; s < cnt; s += kSThreads) {
-        const u64 g = gbase[sdig[s]];
-        if (g == kSkip) continue;
-        const u64* sp = stage + (u64)perm[s] * RW;
-        u64* d = dstb + (g + s) * RW;
-        for (u32 w = 0; w < RW; w++) __stcs(d + w, sp[w]);
+      __syncthreads();
+      // per-warp counters back to zero for the next tile (nothing reads them before then)
+      for (u32 v = tid; v < nd; v += kSThreads) {
+#pragma unroll
+        for (int w = 0; w < kSWarps; w++) whist[w * WS + v] = 0;
       }
+      // write the tile in digit order: consecutive slots of one digit go to consecutive records
+      if (RW == 2) {
+        for (u32 s = tid; s < cnt; s += kSThreads) {
+          const u64 g = gbase[sdig[s]];
+          if (g == kSkip) continue;
+          const ulonglong2 v = *reinterpret_cast<const ulonglong2*>(stage + 2 * (u32)perm[s]);
+          __stcs(reinterpret_cast<ulonglong2*>(dstb + 2 * (g + s)), v);
+        }
+      } else {
+        for (u32 s = tid; s < cnt; s += kSThreads) {
+          const u64 g = gbase[sdig[s]];
+          if (g == kSkip) continue;
+          const u64* sp = stage + (u64)perm[s] * RW;
+          u64* d = dstb + (g + s) * RW;
+          for (u32 w = 0; w < RW; w++) __stcs(d + w, sp[w]);
+        }
+      }
+      __syncthreads();
     }
-    __syncthreads();
   }
 }
 
@@ -800,18 +735,15 @@ __global__ void __launch_bounds__(kThreads) k_classify(Job j, int level) {
         u32 nlo, nW;
         plan_digit(c, p, j.chunk_max, j.wmax, &nlo, &nW);
         const u32 nnd = 1u << nW;
-        const u64 tiles = ceil_div(c, j.T);
         const u64 idx = atomicAdd(&ctl->nbins[N], 1ull);
         const u64 bo = atomicAdd(&ctl->base_used[N], (u64)nnd);
-        const u64 so = atomicAdd(&ctl->status_used[N], tiles * nnd);
-        if (idx >= j.cap_bins || bo + nnd > j.cap_base || so + tiles * nnd > j.cap_status) {
+        if (idx >= j.cap_bins || bo + nnd > j.cap_base) {
           atomicOr(&ctl->err, kErrOverflow);
         } else {
           Bin nbn = {};
           nbn.begin = rb;
           nbn.size = c;
           nbn.base_off = bo;
-          nbn.status_off = so;
           nbn.kand[0] = nbn.kand[1] = ~0ull;
           nbn.lo = nlo;
           nbn.W = nW;
@@ -887,13 +819,11 @@ __global__ void __launch_bounds__(kThreads) k_classify(Job j, int level) {
     __threadfence();
     finalize_list(j, N);
     if (tid == 0) {
-      ctl->s_ticket = 0;
       ctl->cls_done = 0;
       ctl->nredo = 0;
       ctl->nbins[L] = 0;
       ctl->ntiles[L] = 0;
       ctl->base_used[L] = 0;
-      ctl->status_used[L] = 0;
       __threadfence();
     }
   }
@@ -949,7 +879,7 @@ static cudaError_t scatter_it(const Job& j, int level, u32 grid, cudaStream_t s,
   }
 }
 
-int scatter_ctas_per_sm(const Job& j, bool) {
+int scatter_ctas_per_sm(const Job& j) {
   int n = 1;
   if (j.KW == 1) scatter_it<1>(j, 0, 0, 0, &n);
   else scatter_it<2>(j, 0, 0, 0, &n);
@@ -992,8 +922,9 @@ int launch_init_segments(const Job& j, u32 grid, cudaStream_t s) {
   return cudaGetLastError() == cudaSuccess ? 3 : -1;
 }
 
-int launch_hist(const Job& j, int level, int mode, u32 grid, cudaStream_t s) {
+int launch_hist(const Job& j, int level, int mode, cudaStream_t s) {
   const size_t sm = hist_smem(j);
+  const u32 grid = j.lanes;  // one CTA per lane (the scatter pass uses the same lanes)
   if (j.KW == 1) {
     cudaFuncSetAttribute(k_hist<1>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
     k_hist<1><<<grid, kThreads, sm, s>>>(j, level, mode);
@@ -1004,7 +935,7 @@ int launch_hist(const Job& j, int level, int mode, u32 grid, cudaStream_t s) {
   return cudaGetLastError() == cudaSuccess ? 1 : -1;
 }
 
-int launch_scatter(const Job& j, int level, bool, u32 grid, cudaStream_t s) {
+int launch_scatter(const Job& j, int level, u32 grid, cudaStream_t s) {
   cudaError_t e = j.KW == 1 ? scatter_it<1>(j, level, grid, s, nullptr) : scatter_it<2>(j, level, grid, s, nullptr);
   return e == cudaSuccess ? 1 : -1;
 }

@@ -1,7 +1,8 @@
-"""Failure detection on the GPU without a fault: a device-side wait that can never be
-satisfied must end by its bound, report RS_ERR_DEVICE_TIMEOUT, and leave the context usable
-(-m gpu).  The stall is injected through the test entry point: the first look-back wait of
-the pass polls a word nothing writes."""
+"""Failure detection on the GPU without a fault (-m gpu).  The path has no device-side waits;
+what the device can find wrong is a destination outside its bin (corrupted counts) or a list
+that outgrows its bound.  Such a run is reported (RS_ERR_INTERNAL / RS_ERR_QUEUE_OVERFLOW)
+and not written, and the context stays usable.  The test entry point makes one run fail its
+range check on purpose; bad segment offsets are caught the same way."""
 import numpy as np
 import pytest
 
@@ -14,20 +15,17 @@ from tests.gpu_checks import from_dev, to_dev  # noqa: E402
 pytestmark = pytest.mark.gpu
 
 
-def test_stalled_wait_times_out_and_context_survives():
+def test_failed_range_check_is_reported_and_context_survives():
     rng = np.random.default_rng(21)
     a = rng.integers(0, 256, size=(200_000, 16), dtype=np.uint8)
-    old = rg.get_plan()
     try:
-        rg.set_plan(**{**old, "watchdog_polls": 2000})
         assert rg.lib().radix_sort_test_inject(1) == 0
         t = to_dev(a)
         rg.sort(t, 8)
-        assert rg.status() == 7  # RS_ERR_DEVICE_TIMEOUT
-        assert rg.status() == 0  # reported once, then cleared
+        assert rg.status() == 10  # RS_ERR_INTERNAL
+        assert rg.status() == 0   # reported once, then cleared
     finally:
         rg.lib().radix_sort_test_inject(0)
-        rg.set_plan(**old)
     # the context still works and the next call is correct
     t = to_dev(a)
     rg.sort(t, 8)

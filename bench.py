@@ -16,6 +16,7 @@ all ranks / the slowest rank's time.
 from __future__ import annotations
 
 import argparse
+import collections
 import glob
 import hashlib
 import json
@@ -63,6 +64,9 @@ def parse():
     p.add_argument("--duration", type=float, default=60.0, help="served: seconds of arrivals")
     p.add_argument("--saturate", type=int, default=2000, help="served: requests in the saturated runs")
     p.add_argument("--cap-gb", type=float, default=120.0, help="served: HBM admission cap")
+    p.add_argument("--no-out-ring", dest="out_ring", action="store_false",
+                   help="served: let the server allocate a pinned result tensor per request instead of "
+                        "writing results into a reused pinned ring (as the serial path reuses one buffer)")
     p.add_argument("--plan", default="", help="tuning knobs, e.g. digit_bits_max=9,tile_records=2048")
     return p.parse_args()
 
@@ -374,6 +378,7 @@ def served(args):
 
     def serial(idx, paced):
         lat, t0 = [], time.perf_counter()
+        rec = []  # (wait, service, bytes) per request
         with torch.cuda.stream(stream):
             for i in idx:
                 if paced:
@@ -381,6 +386,7 @@ def served(args):
                     if wait > 0:
                         time.sleep(wait)
                 arr = t0 + t_arr[i] if paced else t0
+                start = time.perf_counter()
                 h = req(i)
                 n, R = h.shape
                 d = d_in[:n * R].view(n, R)
@@ -388,11 +394,33 @@ def served(args):
                 rg.sort(d, K, tmp=d_tmp[:n * R].view(n, R), stream=stream)
                 h_out[:n * R].view(n, R).copy_(d, non_blocking=True)
                 stream.synchronize()
-                lat.append(time.perf_counter() - arr)
+                done = time.perf_counter()
+                lat.append(done - arr)
+                rec.append((start - arr, done - start, n * R))
+        slow = sorted(rec, key=lambda x: x[0] + x[1])[-max(1, len(rec) // 100):]
+        serial.info = {"slowest_1pct": {"wait_ms": 1e3 * statistics.mean(x[0] for x in slow),
+                                        "service_ms": 1e3 * statistics.mean(x[1] for x in slow),
+                                        "mbytes": statistics.mean(x[2] for x in slow) / 1e6}}
         return lat, time.perf_counter() - t0
 
+    # results land in a ring of pinned host memory (the serial path reuses one buffer the same
+    # way); a region is handed out again only after the request that held it has finished
+    ring = torch.empty(max(hi * 32 * 4, 16 << 30), dtype=torch.uint8, pin_memory=True) if args.out_ring else None
+    held = collections.deque()  # (start, end, future) of results still being produced
+    ring_pos = [0]
+
+    def ring_take(nbytes):
+        p = (ring_pos[0] + 4095) & ~4095  # page-aligned destinations
+        if p + nbytes > ring.numel():
+            p = 0
+        while held and (held[0][2].done() or not (p + nbytes <= held[0][0] or p >= held[0][1])):
+            held[0][2].result()  # wait (rarely) for the oldest result still in the way
+            held.popleft()
+        ring_pos[0] = p + nbytes
+        return p
+
     def server(idx, paced):
-        with Server(cap_bytes=int(args.cap_gb * 1e9), device=dev) as srv:
+        with Server(cap_bytes=int(args.cap_gb * 1e9), device=dev, timing=True) as srv:
             for R in (8, 16, 32):  # reserve every lane's workspace before the clock starts
                 for ln in srv.lanes:
                     srv._reserve(ln, R, K)
@@ -416,13 +444,34 @@ def served(args):
                     wait = t0 + t_arr[i] - time.perf_counter()
                     if wait > 0:
                         time.sleep(wait)
-                srv.submit(req(i), K, arrival=t0 + t_arr[i] if paced else t0).add_done_callback(finished)
+                h = req(i)
+                if ring is not None:
+                    nb = h.numel()
+                    p = ring_take(nb)
+                    f = srv.submit(h, K, arrival=t0 + t_arr[i] if paced else t0, out=ring[p:p + nb].view(h.shape))
+                    held.append((p, p + nb, f))
+                else:
+                    f = srv.submit(h, K, arrival=t0 + t_arr[i] if paced else t0)
+                f.add_done_callback(finished)
             all_done.wait()
             t1 = time.perf_counter()
             if errors:
                 raise errors[0]
             lat = [done - arr for (_, _, arr, _, done) in srv.completed]
-            info = {"groups": srv.groups, "peak_in_use_gb": srv.peak_in_use / 1e9}
+            # where the slowest 1% spent their time: waiting for admission, or being served
+            slow = sorted(srv.completed, key=lambda c: c[4] - c[2])[-max(1, len(srv.completed) // 100):]
+            info = {"groups": srv.groups, "peak_in_use_gb": srv.peak_in_use / 1e9,
+                    "slowest_1pct": {"wait_ms": 1e3 * statistics.mean(c[3] - c[2] for c in slow),
+                                     "service_ms": 1e3 * statistics.mean(c[4] - c[3] for c in slow),
+                                     "mbytes": statistics.mean(c[0] * c[1] for c in slow) / 1e6}}
+            gt = sorted(srv.group_times, key=lambda g: g[2] + g[3] + g[4])[-max(1, len(srv.group_times) // 100):]
+            if gt:
+                info["slowest_1pct_groups"] = {"records": statistics.mean(g[0] for g in gt),
+                                               "launch_ms": 1e3 * statistics.mean(g[1] for g in gt),
+                                               "copy_in_ms": statistics.mean(g[2] for g in gt),
+                                               "sort_ms": statistics.mean(g[3] for g in gt),
+                                               "copy_out_ms": statistics.mean(g[4] for g in gt)}
+                info["launch_ms_max"] = 1e3 * max(g[1] for g in srv.group_times)
         return lat, t1 - t0, info
 
     # one warm-up pass of a few requests through both paths
@@ -433,6 +482,7 @@ def served(args):
     sat_records = int(sizes[sat].sum())
     with ClockSampler(0) as clk:
         s_lat, s_wall = serial(list(range(m)), True)
+        s_info = serial.info
         v_lat, v_wall, v_info = server(list(range(m)), True)
         s_sat_lat, s_sat_wall = serial(sat, False)
         v_sat_lat, v_sat_wall, v_sat_info = server(sat, False)
@@ -448,7 +498,7 @@ def served(args):
         "latency_ms": {"p50": pct(v_lat, 50), "p99": pct(v_lat, 99), "serial_p50": pct(s_lat, 50),
                        "serial_p99": pct(s_lat, 99)},
         "paced": {"server_records_per_s": total / v_wall, "serial_records_per_s": total / s_wall,
-                  "server": v_info},
+                  "server": v_info, "serial": s_info},
         "saturated": {"server_records_per_s": sat_records / v_sat_wall, "serial_records_per_s": sat_records / s_sat_wall,
                       "server_p99_ms": pct(v_sat_lat, 99), "serial_p99_ms": pct(s_sat_lat, 99),
                       "server": v_sat_info},

@@ -19,15 +19,20 @@
 
 namespace rsg {
 
-constexpr int kCThreads = 1024;  // threads of a chunk CTA (one CTA per SM)
+// Two shapes of the chunk CTA: one CTA of 1,024 threads per SM whose next chunk streams into
+// a second stage buffer while the current one is sorted (kChunkStages = 2), or two CTAs of 512
+// threads per SM with one stage buffer each, which overlap each other (kChunkStages = 1).
+constexpr int kChunkStages = 1;
+constexpr int kCThreads = kChunkStages == 2 ? 1024 : 512;  // threads of a chunk CTA
+constexpr int kChunkCtas = kChunkStages == 2 ? 1 : 2;       // chunk CTAs per SM
 constexpr int kCWarps = kCThreads / 32;
 constexpr int kEsMax = 48;       // largest bucket finished by enumeration sort
 constexpr int kWinBits = 12;     // digit of the on-chip distribution pass
 constexpr int kIdxBits = 13;     // input positions of a chunk (chunk_max <= 2^13)
-constexpr int kChunkItems = 8;   // positions per thread (chunk_max <= 1024 * 8)
+constexpr int kChunkItems = kChunkStages == 2 ? 8 : 10;  // positions per thread (chunk_max <= kCThreads * this)
 constexpr int kCntWords = 1 << (kIdxBits - 1);  // two 16-bit counters per word
 // shared memory of the chunk CTA, and the part that is not per record
-constexpr size_t kChunkSmem = 220 * 1024;
+constexpr size_t kChunkSmem = kChunkStages == 2 ? 220 * 1024 : 108 * 1024;
 constexpr size_t kChunkFixed = kCntWords * 4 + 4 * 1024;
 
 struct ChunkLayout {
@@ -37,7 +42,7 @@ struct ChunkLayout {
 __host__ __device__ inline ChunkLayout chunk_layout(u32 m, u32 RW) {
   ChunkLayout c;
   size_t o = 0;
-  c.stage = o; o += 2 * (size_t)m * RW * 8;  // two stage buffers: the next chunk streams in
+  c.stage = o; o += kChunkStages * (size_t)m * RW * 8;  // stage buffer(s) of the records
   c.perm = o; o += (size_t)m * 2;
   c.out = o; o += (size_t)m * 2;
   o = (o + 15) & ~(size_t)15;
@@ -259,10 +264,10 @@ __device__ u32 range_top_bit(const ChunkCtx<KW, RWT>& c, u32 a, u32 s, bool thro
   return p;
 }
 
-// One CTA per SM: while a chunk is sorted, the next chunk's records stream into the other
-// stage buffer.
+// Persistent CTAs take chunks by ticket.  With two stage buffers the next chunk's records
+// stream in while the current chunk is sorted; with one, the CTAs sharing an SM overlap.
 template <int KW, int RWT>
-__global__ void __launch_bounds__(kCThreads, 1) k_chunk(Job j) {
+__global__ void __launch_bounds__(kCThreads, kChunkCtas) k_chunk(Job j) {
   Ctl* ctl = j.ctl;
   const u64 nch = ctl->nchunks;
   if (nch == 0) return;
@@ -309,19 +314,28 @@ __global__ void __launch_bounds__(kCThreads, 1) k_chunk(Job j) {
   for (u32 i = tid; i < (u32)kCntWords; i += kCThreads) c.cnt[i] = 0;
   if (tid == 0) {
     fetch(0, atomicAdd(&ctl->chunk_ticket, 1ull));
-    fetch(1, atomicAdd(&ctl->chunk_ticket, 1ull));
+    if (kChunkStages == 2) fetch(1, atomicAdd(&ctl->chunk_ticket, 1ull));
   }
   __syncthreads();
-  issue(0);
-  issue(1);
+  if (kChunkStages == 2) {
+    issue(0);
+    issue(1);
+  }
   int cur = 0;
   for (;;) {
-    cp_async_wait_one();
-    __syncthreads();
+    if (kChunkStages == 2) {
+      cp_async_wait_one();
+      __syncthreads();
+    }
     if (s_t[cur] >= nch) break;  // tickets are taken in order: no later chunk either
     const Chunk ch = s_ch[cur];
+    if (kChunkStages == 1) issue(cur);
     u64 nt = 0;
     if (tid == 0) nt = atomicAdd(&ctl->chunk_ticket, 1ull);  // described during this chunk
+    if (kChunkStages == 1) {
+      cp_async_wait_all();
+      __syncthreads();
+    }
     const u32 sz = ch.size;
     c.stage = stage0 + (size_t)cur * m * RW;
     const u64* stage = c.stage;
@@ -400,8 +414,10 @@ __global__ void __launch_bounds__(kCThreads, 1) k_chunk(Job j) {
       if (tid == 0) fetch(cur, nt);
     }
     __syncthreads();  // stage buffer `cur` is free and s_ch[cur] describes the next chunk
-    issue(cur);
-    cur ^= 1;
+    if (kChunkStages == 2) {
+      issue(cur);
+      cur ^= 1;
+    }
   }
   cp_async_wait_all();
 }
@@ -487,7 +503,7 @@ int launch_copy(const Job& j, u32 grid, cudaStream_t s) {
 // fit the shared memory of the chunk CTA (and whose positions fit kIdxBits bits).
 u32 chunk_capacity(u32 RW) {
   const size_t budget = kChunkSmem - kChunkFixed;
-  u32 m = (u32)(budget / (2 * RW * 8 + 4));  // two copies of the record + two u16 index arrays
+  u32 m = (u32)(budget / (kChunkStages * RW * 8 + 4));  // staged copies of the record + two u16 index arrays
   m &= ~63u;
   if (m > (u32)kCThreads * kChunkItems) m = kCThreads * kChunkItems;
   if (m > (1u << kIdxBits)) m = 1u << kIdxBits;

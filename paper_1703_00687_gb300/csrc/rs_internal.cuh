@@ -350,6 +350,13 @@ __device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commi
 // wait until at most one (the most recent) group of this thread's copies is still pending
 __device__ __forceinline__ void cp_async_wait_one() { asm volatile("cp.async.wait_group 1;\n" ::: "memory"); }
 
+// Ask for [p, p + bytes) to be brought into L2 with one bulk request (the range shrunk to
+// 16-byte boundaries, so nothing outside it is touched).  Nothing waits for it.
+__device__ __forceinline__ void prefetch_l2(const void* p, u64 bytes) {
+  const uintptr_t a = ((uintptr_t)p + 15) & ~(uintptr_t)15, e = ((uintptr_t)p + bytes) & ~(uintptr_t)15;
+  if (e > a) asm volatile("cp.async.bulk.prefetch.L2.global [%0], %1;" ::"l"(a), "r"((unsigned)(e - a)) : "memory");
+}
+
 // Start copying `words` 8-byte words global -> shared (16-byte copies when the source is
 // 16-byte aligned; the destination always is).  Call cp_async_wait_all + __syncthreads
 // before reading them.

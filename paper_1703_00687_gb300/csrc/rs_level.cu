@@ -520,6 +520,9 @@ __global__ void __launch_bounds__(kSThreads, 2) k_scatter(Job j, int level) {
       u64* dstb = j.buf[parity ^ 1];
 
       load_words_async<kSThreads>(stage, j.buf[parity] + (begin + r0) * RW, (u64)cnt * RW);
+      // the lane's next tile of this bin comes into L2 while this one is processed
+      if (tid == 0 && t + 1 < t1 && r0 + T < size)
+        prefetch_l2(j.buf[parity] + (begin + r0 + T) * RW, min((u64)T, size - r0 - T) * RW * 8);
       if (b != cur) {  // first tile of this lane's part of the bin: its run starts
         cur = b;
         const u64* sg = j.seg + ((ln + b) << j.wmax);
@@ -696,6 +699,12 @@ __global__ void __launch_bounds__(kThreads) k_classify(Job j, int level) {
   __shared__ u8 cls[1 << kWMax];
   __shared__ u32 cnt[1 << kWMax];
   __shared__ u64 boff[1 << kWMax];
+  // the bin's chunks, packed by thread 0, then reserved with one atomic and written by all
+  __shared__ u32 pk_first[1 << kWMax];  // first sub-bin | (1 << 31) if any needs sorting
+  __shared__ u16 pk_last[1 << kWMax];   // last sub-bin
+  __shared__ u32 pk_size[1 << kWMax];
+  __shared__ u32 s_npk;
+  __shared__ u64 s_base;
   __shared__ int s_last;
   const int tid = threadIdx.x;
   for (u64 b = blockIdx.x; b < nb; b += gridDim.x) {
@@ -756,29 +765,16 @@ __global__ void __launch_bounds__(kThreads) k_classify(Job j, int level) {
     }
     __syncthreads();
     if (tid == 0) {
-      // greedy packing of consecutive small sub-bins into on-chip chunks
-      u64 cb = 0;
-      u32 csz = 0, nsub = 0, vfirst = 0, vlast = 0;
+      // greedy packing of consecutive small sub-bins into on-chip chunks (a chunk made only
+      // of single records, already in `in`, is finished and not kept)
+      u32 npk = 0, csz = 0, vfirst = 0, vlast = 0;
       bool open = false, uns = false;
       auto emit = [&]() {
         if (open && (uns || p1)) {
-          const u64 idx = atomicAdd(&ctl->nchunks, 1ull);
-          if (idx >= j.cap_chunks) {
-            atomicOr(&ctl->err, kErrOverflow);
-          } else {
-            Chunk ch = {};
-            ch.begin = bin.begin + cb;
-            ch.size = csz;
-            ch.flags = (p1 ? kChSrcTmp : 0u) | (uns ? 0u : kChCopyOnly);
-            // one sub-bin shares every bit >= lo; several differ in the digit itself
-            ch.p = bin.lo;
-            ch.pw = (u16)bin.W;
-            ch.v0 = vfirst;
-            u32 sb = 0;
-            while ((1u << sb) < vlast - vfirst + 1) sb++;
-            ch.sb = (u16)(nsub == 1 ? 0 : sb);
-            j.chunks[idx] = ch;
-          }
+          pk_first[npk] = vfirst | (uns ? 0x80000000u : 0u);
+          pk_last[npk] = (u16)vlast;
+          pk_size[npk] = csz;
+          npk++;
         }
         open = false;
       };
@@ -789,15 +785,12 @@ __global__ void __launch_bounds__(kThreads) k_classify(Job j, int level) {
           const u32 sz = cnt[v];
           if (open && csz + sz > j.chunk_max) emit();
           if (!open) {
-            cb = boff[v];
             csz = 0;
-            nsub = 0;
             vfirst = v;
             uns = false;
             open = true;
           }
           csz += sz;
-          nsub++;
           vlast = v;
           if (k == 2) uns = true;
         } else {
@@ -805,6 +798,33 @@ __global__ void __launch_bounds__(kThreads) k_classify(Job j, int level) {
         }
       }
       emit();
+      s_npk = npk;
+      s_base = npk ? atomicAdd(&ctl->nchunks, (u64)npk) : 0;
+    }
+    __syncthreads();
+    {
+      const u32 npk = s_npk;
+      const u64 base = s_base;
+      if (base + npk > j.cap_chunks) {
+        if (tid == 0 && npk) atomicOr(&ctl->err, kErrOverflow);
+      } else {
+        for (u32 q = tid; q < npk; q += kThreads) {
+          const u32 vf = pk_first[q] & 0x7fffffffu, vl = pk_last[q];
+          const bool uns = (pk_first[q] >> 31) != 0;
+          Chunk ch = {};
+          ch.begin = bin.begin + boff[vf];
+          ch.size = pk_size[q];
+          ch.flags = (p1 ? kChSrcTmp : 0u) | (uns ? 0u : kChCopyOnly);
+          // one sub-bin shares every bit >= lo; several differ in the digit itself
+          ch.p = bin.lo;
+          ch.pw = (u16)bin.W;
+          ch.v0 = vf;
+          u32 sb = 0;
+          while ((1u << sb) < vl - vf + 1) sb++;
+          ch.sb = (u16)(vl == vf ? 0 : sb);
+          j.chunks[base + q] = ch;
+        }
+      }
     }
     __syncthreads();
   }

@@ -3,7 +3,8 @@
 Requests (host record arrays) arrive at any time.  A scheduler thread admits them in arrival
 order while the device memory they need fits under the cap, groups waiting requests with the
 same record layout into one segmented sort, and runs each group on one of several CUDA
-streams ("lanes"), so that the copies and kernels of different groups overlap on the device.
+streams ("lanes"), with its copies on one copy-in and one copy-out stream shared by all
+lanes, so that the copies and kernels of different groups overlap on the device.
 A request's future resolves to its sorted records on the host.
 
 The sort is stable and every segment of a segmented call is sorted on its own, so a
@@ -80,9 +81,13 @@ def form_group(pending, free_bytes: int, max_records: int, max_requests: int, fo
 
 
 class _Lane:
-    def __init__(self, torch, device):
+    def __init__(self, torch, device, timing):
         self.stream = torch.cuda.Stream(device=device)
-        self.event = torch.cuda.Event()
+        self.in_start = torch.cuda.Event(enable_timing=timing)  # the group's copy-in may start
+        self.in_done = torch.cuda.Event(enable_timing=timing)   # the group's input is on the device
+        self.sorted = torch.cuda.Event(enable_timing=timing)    # the group is sorted
+        self.event = torch.cuda.Event(enable_timing=timing)     # the group's results are on the host
+        self.launch_s = 0.0
         self.group = None
         self.hold = None        # device tensors of the running group
         self.bytes = 0
@@ -97,7 +102,7 @@ class Server:
     """
 
     def __init__(self, cap_bytes: int = 120 * 10 ** 9, lanes: int = 4, max_group_records: int = 128 * 10 ** 6,
-                 max_group_requests: int = 256, device=None, poll_s: float = 20e-6):
+                 max_group_requests: int = 256, device=None, poll_s: float = 20e-6, timing: bool = False):
         import torch
 
         self.torch = torch
@@ -106,11 +111,15 @@ class Server:
         self.max_records = int(max_group_records)
         self.max_requests = int(max_group_requests)
         self.poll_s = poll_s
-        self.lanes = [_Lane(torch, self.device) for _ in range(lanes)]
+        self.timing = timing  # per group: copy-in / sort / copy-out times from CUDA events
+        self.lanes = [_Lane(torch, self.device, timing) for _ in range(lanes)]
+        self.copy_in = torch.cuda.Stream(device=self.device)
+        self.copy_out = torch.cuda.Stream(device=self.device)
         self.pending = collections.deque()
         self.in_use = 0
         self.peak_in_use = 0
         self.completed = []      # (records, rec_size, arrival, admitted, done) per finished request
+        self.group_times = []    # timing=True: (records, launch s, copy-in ms, sort ms, copy-out ms) per group
         self.groups = 0
         self._cv = threading.Condition()
         self._closing = False
@@ -120,12 +129,19 @@ class Server:
         self._thread.start()
 
     # ------------------------------------------------------------------ public
-    def submit(self, records, key_size: int = 8, arrival: float | None = None) -> Future:
+    def submit(self, records, key_size: int = 8, arrival: float | None = None, out=None) -> Future:
+        """Queue one sort.  ``out``: optional CPU tensor of the same byte size (pinned memory
+        makes the copy asynchronous) that receives the result; by default a pinned tensor is
+        allocated for it.  The future resolves to the tensor holding the sorted records."""
         if records.dim() != 2 or records.device.type != "cpu":
             raise ValueError("records must be a 2-D CPU tensor (n, rec_size bytes)")
         req = Request(records=records, key_size=key_size, arrival=time.perf_counter() if arrival is None else arrival)
         req.n = int(records.shape[0])
         req.rec_size = int(records.shape[1] * records.element_size())
+        if out is not None:
+            if out.device.type != "cpu" or out.numel() * out.element_size() != req.n * req.rec_size:
+                raise ValueError("out must be a CPU tensor of the same byte size as records")
+            req.out = out
         if group_bytes(req.n, req.rec_size, key_size, 1) > self.cap or req.n > self.max_records:
             req.future.set_exception(ValueError("request larger than the server's admission cap"))
             return req.future
@@ -160,33 +176,53 @@ class Server:
             self._reserved[key] = True
 
     def _launch(self, lane, group):
+        """Three stages on three kinds of stream: the group's host-to-device copies on the
+        shared copy-in stream, its sort on the lane's stream, its device-to-host copies on the
+        shared copy-out stream.  Copies in each direction therefore run one group at a time,
+        in admission order and at the link's full rate, while the sorts of other groups (and
+        the copies the other way) overlap with them."""
         torch = self.torch
         R, K = group[0].layout
         total = sum(r.n for r in group)
         self._reserve(lane, R, K)
         now = time.perf_counter()
-        with torch.cuda.device(self.device), torch.cuda.stream(lane.stream):
-            d_in = torch.empty((total, R), dtype=torch.uint8, device=self.device)
-            d_tmp = torch.empty_like(d_in)
+        with torch.cuda.device(self.device):
+            with torch.cuda.stream(lane.stream):
+                d_in = torch.empty((total, R), dtype=torch.uint8, device=self.device)
+                d_tmp = torch.empty_like(d_in)
             offs, o = [0], 0
             for r in group:
-                d_in[o:o + r.n].copy_(r.records.view(torch.uint8).reshape(r.n, R), non_blocking=True)
                 o += r.n
                 offs.append(o)
             d_offs = None
+            self.copy_in.wait_stream(lane.stream)  # the buffers' allocation is ordered first
+            with torch.cuda.stream(self.copy_in):
+                lane.in_start.record(self.copy_in)
+                o = 0
+                for r in group:
+                    d_in[o:o + r.n].copy_(r.records.view(torch.uint8).reshape(r.n, R), non_blocking=True)
+                    o += r.n
+                if len(group) > 1:
+                    h_offs = torch.tensor(offs, dtype=torch.int64).pin_memory()
+                    d_offs = h_offs.to(self.device, non_blocking=True)
+                lane.in_done.record(self.copy_in)
+            lane.stream.wait_event(lane.in_done)
             if len(group) == 1:
                 sort(d_in, K, tmp=d_tmp, stream=lane.stream)
             else:
-                h_offs = torch.tensor(offs, dtype=torch.int64).pin_memory()
-                d_offs = h_offs.to(self.device, non_blocking=True)
                 sort_segmented(d_in, d_offs, K, tmp=d_tmp, stream=lane.stream, total=total)
-            o = 0
-            for r in group:
-                r.out = torch.empty((r.n, R), dtype=torch.uint8, pin_memory=True)
-                r.out.copy_(d_in[o:o + r.n], non_blocking=True)
-                r.admitted = now
-                o += r.n
-            lane.event.record(lane.stream)
+            lane.sorted.record(lane.stream)
+            self.copy_out.wait_event(lane.sorted)
+            with torch.cuda.stream(self.copy_out):
+                o = 0
+                for r in group:
+                    if r.out is None:
+                        r.out = torch.empty((r.n, R), dtype=torch.uint8, pin_memory=True)
+                    r.out.view(torch.uint8).reshape(r.n, R).copy_(d_in[o:o + r.n], non_blocking=True)
+                    r.admitted = now
+                    o += r.n
+                lane.event.record(self.copy_out)
+        lane.launch_s = time.perf_counter() - now
         lane.group = group
         lane.hold = (d_in, d_tmp, d_offs)
         lane.bytes = group_bytes(total, R, K, len(group))
@@ -205,6 +241,10 @@ class Server:
             else:
                 r.future.set_result(out)
             self.completed.append((r.n, r.rec_size, r.arrival, r.admitted, r.done))
+        if self.timing:
+            self.group_times.append((sum(r.n for r in lane.group), lane.launch_s,
+                                     lane.in_start.elapsed_time(lane.in_done), lane.in_done.elapsed_time(lane.sorted),
+                                     lane.sorted.elapsed_time(lane.event)))
         self.in_use -= lane.bytes
         lane.group, lane.hold, lane.bytes = None, None, 0
 

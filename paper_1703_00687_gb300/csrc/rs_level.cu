@@ -413,7 +413,7 @@ constexpr int kSWarps = kSThreads / 32;
 // Shared memory of k_scatter: T records, per-warp 16-bit digit counters (row stride 2^wmax),
 // the tile's permutation, per-digit counts / run bases / global bases.
 struct ScatterLayout {
-  size_t stage, whist, perm, sdig, tcount, tbase, gbase, total;
+  size_t stage, whist, slot, tbase, gbase, total;
 };
 
 __host__ __device__ inline ScatterLayout scatter_layout(u32 T, u32 RW, u32 wmax) {
@@ -422,10 +422,8 @@ __host__ __device__ inline ScatterLayout scatter_layout(u32 T, u32 RW, u32 wmax)
   size_t o = 0;
   s.stage = o; o += (size_t)T * RW * 8;
   s.whist = o; o += (size_t)kSWarps * nd * 2;
-  s.perm = o; o += (size_t)T * 2;
-  s.sdig = o; o += (size_t)T * 2;
+  s.slot = o; o += (size_t)T * 4;
   o = (o + 15) & ~(size_t)15;
-  s.tcount = o; o += nd * 4;
   s.tbase = o; o += nd * 4;
   s.gbase = o; o += nd * 8;
   s.total = (o + 127) & ~(size_t)127;
@@ -451,6 +449,37 @@ __device__ __forceinline__ u32 staged_digit(const u64* rec, u32 lo, u32 W) {
   k.w[0] = rec[0];
   if (KW == 2) k.w[KW - 1] = rec[1];
   return digit_of<KW>(k, lo, W);
+}
+
+// Digits per thread in the scatter's prefix pass: nd / kSThreads, at least 2 (the per-warp
+// counters are read two at a time).
+__device__ __forceinline__ u32 digits_per_thread(u32 nd) { return nd > 2u * kSThreads ? nd / kSThreads : 2u; }
+
+// Exclusive prefix sum over the CTA of one value per thread (NT threads); ends with a barrier.
+template <int NT>
+__device__ __forceinline__ u32 block_exclusive_sum(u32 x, u32* scr) {
+  constexpr int kW = NT / 32;
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  u32 incl = x;
+#pragma unroll
+  for (int o = 1; o < 32; o <<= 1) {
+    const u32 y = __shfl_up_sync(kFull, incl, o);
+    if (lane >= o) incl += y;
+  }
+  if (lane == 31) scr[warp] = incl;
+  __syncthreads();
+  if (warp == 0) {
+    const u32 v = lane < kW ? scr[lane] : 0;
+    u32 t = v;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+      const u32 y = __shfl_up_sync(kFull, t, o);
+      if (lane >= o) t += y;
+    }
+    if (lane < kW) scr[lane] = t - v;
+  }
+  __syncthreads();
+  return scr[warp] + incl - x;
 }
 
 constexpr u64 kSkip = ~0ull;  // gbase of a digit whose run would leave its bin
@@ -485,9 +514,7 @@ __global__ void __launch_bounds__(kSThreads, 2) k_scatter(Job j, int level) {
   extern __shared__ __align__(16) unsigned char smem[];
   u64* stage = (u64*)(smem + lay.stage);
   u16* whist = (u16*)(smem + lay.whist);
-  u16* perm = (u16*)(smem + lay.perm);
-  u16* sdig = (u16*)(smem + lay.sdig);
-  u32* tcount = (u32*)(smem + lay.tcount);
+  u32* slotw = (u32*)(smem + lay.slot);  // per output slot: staged record | digit << 16
   u32* tbase = (u32*)(smem + lay.tbase);
   u64* gbase = (u64*)(smem + lay.gbase);
   __shared__ u32 scan_scr[kSWarps + 1];
@@ -526,10 +553,11 @@ __global__ void __launch_bounds__(kSThreads, 2) k_scatter(Job j, int level) {
       if (b != cur) {  // first tile of this lane's part of the bin: its run starts
         cur = b;
         const u64* sg = j.seg + ((ln + b) << j.wmax);
+        const u32 D = digits_per_thread(nd);
 #pragma unroll
         for (u32 q = 0; q < kDigitsPerThread; q++) {
-          const u32 v = tid + q * kSThreads;
-          run[q] = v < nd ? sg[v] : 0;
+          const u32 v = D * tid + q;
+          run[q] = (q < D && v < nd) ? sg[v] : 0;
         }
       }
       cp_async_wait_all();
@@ -573,31 +601,48 @@ __global__ void __launch_bounds__(kSThreads, 2) k_scatter(Job j, int level) {
         }
       }
       __syncthreads();
-      for (u32 v = tid; v < nd; v += kSThreads) {
-        u32 acc = 0;
+      // Thread tid owns digits [D*tid, D*tid + D): it turns their per-warp counts into each
+      // warp's offset inside the digit's run (two 16-bit counters per 32-bit access), then one
+      // block scan of the threads' totals gives the digits' first slots in the tile.
+      const u32 D = digits_per_thread(nd);
+      const u32 v0 = D * tid;
+      u32 c[kDigitsPerThread];
 #pragma unroll
-        for (int w = 0; w < kSWarps; w++) {
-          const u32 x = whist[w * WS + v];
-          whist[w * WS + v] = (u16)acc;
-          acc += x;
+      for (u32 q = 0; q < kDigitsPerThread; q++) c[q] = 0;
+      if (v0 < nd) {
+        u32* wh32 = (u32*)whist;
+#pragma unroll
+        for (u32 p2 = 0; p2 < kDigitsPerThread / 2; p2++) {
+          if (2 * p2 >= D) break;
+          u32 a0 = 0, a1 = 0;
+#pragma unroll
+          for (int w = 0; w < kSWarps; w++) {
+            u32* x = wh32 + w * (WS >> 1) + (v0 >> 1) + p2;
+            const u32 y = *x;
+            *x = a0 | (a1 << 16);
+            a0 += y & 0xffffu;
+            a1 += y >> 16;
+          }
+          c[2 * p2] = a0;
+          c[2 * p2 + 1] = a1;
         }
-        tcount[v] = acc;
-        tbase[v] = acc;
       }
-      __syncthreads();
-      block_exclusive_scan<kSThreads>(tbase, nd, scan_scr);
-      // destinations of this tile's runs; a run that would leave its bin (possible only with
+      u32 mine = 0;
+#pragma unroll
+      for (u32 q = 0; q < kDigitsPerThread; q++) mine += c[q];
+      u32 tb = block_exclusive_sum<kSThreads>(mine, scan_scr);
+      // destinations of this thread's runs; a run that would leave its bin (possible only with
       // corrupted counts) is reported and not written
 #pragma unroll
       for (u32 q = 0; q < kDigitsPerThread; q++) {
-        const u32 v = tid + q * kSThreads;
-        if (v >= nd) break;
-        const u32 c = tcount[v];
+        const u32 v = v0 + q;
+        if (q >= D || v >= nd) break;
+        const u32 cq = c[q];
         const u64 first = run[q];
-        run[q] += c;
-        u64 g = begin + first - tbase[v];
-        bool bad = c && (first > size || c > size - first);
-        if (c && inject) {
+        run[q] += cq;
+        u64 g = begin + first - tb;
+        bool bad = cq && (first > size || cq > size - first);
+        if (cq && inject) {
           bad = true;
           inject = false;
         }
@@ -605,15 +650,17 @@ __global__ void __launch_bounds__(kSThreads, 2) k_scatter(Job j, int level) {
           atomicOr(&ctl->err, kErrInternal);
           g = kSkip;
         }
+        tbase[v] = tb;
         gbase[v] = g;
+        tb += cq;
       }
+      __syncthreads();
       if (cnt == T) {
 #pragma unroll
         for (int it = 0; it < IT; it++) {
           const u32 d = packed[it] >> 16;
           const u32 slot = tbase[d] + wh[d] + (packed[it] & 0xffffu);
-          perm[slot] = (u16)(warp * PW + it * 32 + lane);
-          sdig[slot] = (u16)d;
+          slotw[slot] = (warp * PW + it * 32 + lane) | (d << 16);
         }
       } else {
 #pragma unroll
@@ -621,8 +668,7 @@ __global__ void __launch_bounds__(kSThreads, 2) k_scatter(Job j, int level) {
           if (packed[it] != 0xffffffffu) {
             const u32 d = packed[it] >> 16;
             const u32 slot = tbase[d] + wh[d] + (packed[it] & 0xffffu);
-            perm[slot] = (u16)(warp * PW + it * 32 + lane);
-            sdig[slot] = (u16)d;
+            slotw[slot] = (warp * PW + it * 32 + lane) | (d << 16);
           }
         }
       }
@@ -635,16 +681,18 @@ __global__ void __launch_bounds__(kSThreads, 2) k_scatter(Job j, int level) {
       // write the tile in digit order: consecutive slots of one digit go to consecutive records
       if (RW == 2) {
         for (u32 s = tid; s < cnt; s += kSThreads) {
-          const u64 g = gbase[sdig[s]];
+          const u32 sw = slotw[s];
+          const u64 g = gbase[sw >> 16];
+          const ulonglong2 v = *reinterpret_cast<const ulonglong2*>(stage + 2 * (sw & 0xffffu));
           if (g == kSkip) continue;
-          const ulonglong2 v = *reinterpret_cast<const ulonglong2*>(stage + 2 * (u32)perm[s]);
           __stcs(reinterpret_cast<ulonglong2*>(dstb + 2 * (g + s)), v);
         }
       } else {
         for (u32 s = tid; s < cnt; s += kSThreads) {
-          const u64 g = gbase[sdig[s]];
+          const u32 sw = slotw[s];
+          const u64 g = gbase[sw >> 16];
           if (g == kSkip) continue;
-          const u64* sp = stage + (u64)perm[s] * RW;
+          const u64* sp = stage + (u64)(sw & 0xffffu) * RW;
           u64* d = dstb + (g + s) * RW;
           for (u32 w = 0; w < RW; w++) __stcs(d + w, sp[w]);
         }

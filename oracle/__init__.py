@@ -45,6 +45,8 @@ def lib():
         L.oracle_lsd_sort.argtypes = [vp, vp, u64, u32, u32]
         L.oracle_sort_segmented.restype = i32
         L.oracle_sort_segmented.argtypes = [vp, vp, vp, u64, u32, u32]
+        L.oracle_count_runs.restype = i32
+        L.oracle_count_runs.argtypes = [vp, u64, u32, u32, vp, vp, vp]
         _lib = L
     return _lib
 
@@ -97,3 +99,17 @@ def sort_inplace_raw(ptr: int, tmp_ptr: int, n: int, rec_size: int, key_size: in
     """Sort n records at host address ptr (tmp_ptr: scratch of the same size)."""
     if lib().oracle_lsd_sort(ptr, tmp_ptr, n, rec_size, key_size) != 0:
         raise ValueError("bad oracle_lsd_sort arguments")
+
+
+def count_runs(records: np.ndarray, key_size: int):
+    """Runs of equal keys in consecutive records: (first record of each run, run lengths)."""
+    src = _records(records)
+    n, r = src.shape
+    first = np.empty((max(n, 1), r), dtype=np.uint8)
+    counts = np.zeros(max(n, 1), dtype=np.uint64)
+    nruns = np.zeros(1, dtype=np.uint64)
+    if lib().oracle_count_runs(src.ctypes.data, n, r, key_size, first.ctypes.data, counts.ctypes.data,
+                               nruns.ctypes.data) != 0:
+        raise ValueError("bad oracle_count_runs arguments")
+    m = int(nruns[0])
+    return first[:m], counts[:m]

@@ -96,3 +96,24 @@ int oracle_sort_segmented(uint8_t *buf, uint8_t *tmp, const uint64_t *offsets, u
     }
     return 0;
 }
+
+/* Run-length count of equal keys (the counting step after the sort in k-mer counting, the
+ * paper's application in section 4): a run is a maximal range of consecutive records whose
+ * keys (bytes [0, key_size)) are equal.  first receives the first record of every run,
+ * counts[r] the number of records in run r; *nruns the number of runs.  Returns 0 or -1. */
+int oracle_count_runs(const uint8_t *src, uint64_t n, uint32_t rec_size, uint32_t key_size, uint8_t *first,
+                      uint64_t *counts, uint64_t *nruns) {
+    if (rec_size == 0 || key_size == 0 || key_size > rec_size) return -1;
+    uint64_t r = 0;
+    for (uint64_t i = 0; i < n; i++) {
+        const uint8_t *rec = src + i * rec_size;
+        if (i == 0 || memcmp(rec, rec - rec_size, key_size) != 0) {
+            memcpy(first + r * rec_size, rec, rec_size);
+            counts[r] = 0;
+            r++;
+        }
+        counts[r - 1]++;
+    }
+    *nruns = r;
+    return 0;
+}

@@ -245,3 +245,39 @@ def test_planted_mistakes_fail_a_pin(name):
         assert r.returncode == 0, r.stderr
         n_fail = int(r.stdout.split("FAILURES")[1])
         assert n_fail > 0, f"mutant {name} passed every pin"
+
+
+# ---------------------------------------------------------------- run-length counting (k-mer counting)
+def test_count_runs_closed_forms():
+    # all keys equal: one run of n; all distinct: n runs of 1; key v repeated m_v times: runs m_v
+    a = np.zeros((7, 16), dtype=np.uint8)
+    a[:, 8:] = np.arange(7, dtype=np.uint8)[:, None]  # payload differs, keys equal
+    f, c = oracle.count_runs(a, 8)
+    assert c.tolist() == [7] and np.array_equal(f[0], a[0])
+    b = np.zeros((5, 8), dtype=np.uint8)
+    b[:, 0] = np.arange(5)
+    f, c = oracle.count_runs(b, 8)
+    assert c.tolist() == [1] * 5 and np.array_equal(f, b)
+    mult = [3, 1, 4, 1, 5]
+    keys = np.repeat(np.arange(len(mult), dtype=np.uint64), mult)
+    recs = keys.view(np.uint8).reshape(-1, 8)
+    f, c = oracle.count_runs(recs, 8)
+    assert c.tolist() == mult
+    assert oracle.count_runs(np.zeros((0, 8), dtype=np.uint8), 8)[1].size == 0
+
+
+def test_count_runs_equals_numpy_unique_on_sorted_keys():
+    rng = np.random.default_rng(5)
+    for key_size, rec in ((8, 16), (16, 24), (3, 8)):
+        a = rng.integers(0, 256, size=(3000, rec), dtype=np.uint8)
+        a[:, :key_size] = rng.integers(0, 4, size=(3000, key_size), dtype=np.uint8)  # many repeats
+        s = oracle.sort(a, key_size)
+        f, c = oracle.count_runs(s, key_size)
+        keys = [bytes(r[:key_size]) for r in s]
+        uniq, counts = np.unique(np.array(keys, dtype=object), return_counts=True)
+        # np.unique orders bytes lexicographically, the sort orders little-endian integers:
+        # compare as multisets of (key, count), and check the runs appear in sorted order
+        assert sorted(zip(uniq.tolist(), counts.tolist())) == sorted(zip([bytes(r[:key_size]) for r in f], c.tolist()))
+        assert int(c.sum()) == len(s)
+        ints = [int.from_bytes(bytes(r[:key_size]), "little") for r in f]
+        assert ints == sorted(ints) and len(set(ints)) == len(ints)

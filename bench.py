@@ -42,6 +42,12 @@ WORKLOADS = {
     "served_200rps": ("uniform", 64_000_000, 0, 8, 7,
                       "Poisson arrivals 200/s, sizes log-uniform in [1024, 64e6] records, rec_size in {8,16,32}, "
                       "uniform u64 keys (seed 7)"),
+    "sweep_rec": ("uniform", 0, 0, 0, 11, "record-size sweep: R in 8..64, key 8 or 16 bytes, 16 GB of uniform records each"),
+    "kmer_count": ("kmer", 500_000_000, 24, 16, 4, "k-mer counting: 5e8 records of 16-byte k-mer keys, each of 1.25e8 "
+                                                "distinct k-mers 4 times; sort, then run-length count"),
+    "tiny": ("uniform", 1 << 26, 0, 0, 12, "tiny sorts: 2^26 records split into segments of n = 2..64 records, "
+                                        "uniform keys, one segmented call per (n, layout)"),
+    "sweep_sm": ("uniform", 1_000_000_000, 16, 8, 2, "SM-count sweep of the 1e9 x 16 B uniform sort (grids capped to k SMs)"),
     "batched_1e5_r16": ("uniform", 2_000_000_000, 16, 8, 6,
                         "100,000 segments, log-uniform sizes in [1, 1e6] scaled to sum <= 2e9 (seed 5); uniform u64 "
                         "keys (seed 6), u64 index payload"),
@@ -511,10 +517,163 @@ def served(args):
     return 0
 
 
+def time_sort(rg, torch, pristine, buf, tmp, K, steps, warmup):
+    """Median CUDA-event time (ms) of one sort of the resident input (restored before each)."""
+    stream = torch.cuda.current_stream()
+    for _ in range(warmup):
+        buf.copy_(pristine)
+        rg.sort(buf, K, tmp=tmp, stream=stream)
+    ms = []
+    for _ in range(steps):
+        buf.copy_(pristine)
+        a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        a.record(stream)
+        rg.sort(buf, K, tmp=tmp, stream=stream)
+        b.record(stream)
+        b.synchronize()
+        ms.append(a.elapsed_time(b))
+    if rg.status() != 0:
+        raise SystemExit("device status error")
+    return statistics.median(ms)
+
+
+def sweeps(args):
+    """--workload sweep_rec: records/s and HBM GB/s (of the 7-pass algorithmic bytes at two
+    distribution levels) over record sizes 8..64 bytes with 8- and 16-byte keys, 16 GB of
+    uniform records each (the paper's record-size axis).  --workload sweep_sm: the 1e9 x 16 B
+    sort with its persistent grids capped to k SMs (the paper's thread-scaling axis)."""
+    import torch
+
+    import paper_1703_00687_gb300 as rg
+
+    torch.cuda.set_device(0)
+    peak, peak_src = measured_peaks()
+    rows = []
+    if args.workload == "kmer_count":
+        kind, n, R, K, seed, _ = WORKLOADS["kmer_count"]
+        if args.n:
+            n = args.n
+        D = n // 4
+        h = torch.empty((n, R), dtype=torch.uint8, pin_memory=True)
+        wl.make(kind, n, R, K, seed, out=h)
+        pristine = h.cuda()
+        del h
+        for a in range(D, n, 1 << 26):  # key of record i = key of record i mod D
+            b = min(n, a + (1 << 26))
+            idx = torch.arange(a, b, device="cuda") % D
+            pristine[a:b, :K] = pristine[idx, :K]
+        buf, tmp = torch.empty_like(pristine), torch.empty_like(pristine)
+        stream = torch.cuda.current_stream()
+        t_sort, t_count = [], []
+        for k in range(args.warmup + args.steps):
+            buf.copy_(pristine)
+            e = [torch.cuda.Event(enable_timing=True) for _ in range(3)]
+            e[0].record(stream)
+            rg.sort(buf, K, tmp=tmp, stream=stream)
+            e[1].record(stream)
+            first, counts = rg.count_runs(buf, K, stream=stream)
+            e[2].record(stream)
+            e[2].synchronize()
+            if k >= args.warmup:
+                t_sort.append(e[0].elapsed_time(e[1]))
+                t_count.append(e[1].elapsed_time(e[2]))
+        if rg.status() != 0:
+            raise SystemExit("device status error")
+        runs = first.shape[0]
+        ok = runs == D and bool((counts == 4).all())
+        ms_s, ms_c = statistics.median(t_sort), statistics.median(t_count)
+        count_bytes = 2 * n * R + runs * (R + 8) * 2  # keys read twice; first records and counts written
+        rows.append({"n": n, "distinct": D, "runs": runs, "counts_ok": ok, "sort_ms": ms_s, "count_ms": ms_c,
+                     "count_gbs": count_bytes / (ms_c / 1e3) / 1e9})
+        value = n / ((ms_s + ms_c) / 1e3)
+        metric, unit = "records/s (sort + run-length count)", "records/s"
+    elif args.workload == "tiny":
+        # the paper's tiny-sorter experiment on the GPU: many independent sorts of n records
+        total = args.n or (1 << 26)
+        for R, K in [(8, 8), (16, 8), (24, 8), (32, 8), (16, 16)]:
+            h = torch.empty((total, R), dtype=torch.uint8, pin_memory=True)
+            wl.make("uniform", total, R, K, 12, out=h)
+            pristine = h.cuda()
+            del h
+            buf, tmp = torch.empty_like(pristine), torch.empty_like(pristine)
+            stream = torch.cuda.current_stream()
+            for n in (2, 4, 8, 16, 32, 64):
+                offs = torch.arange(0, total + 1, n, dtype=torch.int64, device="cuda")
+                if int(offs[-1]) != total:
+                    offs = torch.cat([offs, torch.tensor([total], dtype=torch.int64, device="cuda")])
+                ms = []
+                for k in range(args.warmup + args.steps):
+                    buf.copy_(pristine)
+                    a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+                    a.record(stream)
+                    rg.sort_segmented(buf, offs, K, tmp=tmp, stream=stream, total=total)
+                    b.record(stream)
+                    b.synchronize()
+                    if k >= args.warmup:
+                        ms.append(a.elapsed_time(b))
+                if rg.status() != 0:
+                    raise SystemExit("device status error")
+                m = statistics.median(ms)
+                rows.append({"rec_size": R, "key_size": K, "n": n, "ms": m, "ns_per_record": 1e6 * m / total})
+            del pristine, buf, tmp
+            torch.cuda.empty_cache()
+        value = statistics.mean(r["ns_per_record"] for r in rows)
+        metric, unit = "mean time per record over tiny sorts", "ns/record"
+    elif args.workload == "sweep_rec":
+        total_bytes = 16 * 10 ** 9 if not args.n else args.n
+        for R, K in [(8, 8), (16, 8), (16, 16), (24, 8), (24, 16), (32, 8), (32, 16), (48, 16), (64, 16)]:
+            n = total_bytes // R
+            h = torch.empty((n, R), dtype=torch.uint8, pin_memory=True)
+            wl.make("uniform", n, R, K, 11, out=h)
+            pristine = h.cuda()
+            del h
+            buf, tmp = torch.empty_like(pristine), torch.empty_like(pristine)
+            ms = time_sort(rg, torch, pristine, buf, tmp, K, args.steps, args.warmup)
+            b_alg = 7 * n * R
+            rows.append({"rec_size": R, "key_size": K, "n": n, "ms": ms, "records_per_s": n / (ms / 1e3),
+                         "gbs_7pass": b_alg / (ms / 1e3) / 1e9, "frac_7pass": b_alg / (ms / 1e3) / 1e9 / peak})
+            del pristine, buf, tmp
+            torch.cuda.empty_cache()
+        value = statistics.mean(r["frac_7pass"] for r in rows)
+        metric, unit = "mean HBM fraction over record sizes", "fraction"
+    else:
+        kind, n, R, K, seed, _ = WORKLOADS["uniform_1e9_r16"]
+        if args.n:
+            n = args.n
+        h = torch.empty((n, R), dtype=torch.uint8, pin_memory=True)
+        wl.make(kind, n, R, K, seed, out=h)
+        pristine = h.cuda()
+        del h
+        buf, tmp = torch.empty_like(pristine), torch.empty_like(pristine)
+        sms = torch.cuda.get_device_properties(0).multi_processor_count
+        old = rg.get_plan()
+        try:
+            for k in sorted({max(1, sms // 8), sms // 4, sms // 2, (3 * sms) // 4, sms}):
+                rg.set_plan(**{**old, "sm_limit": k})
+                ms = time_sort(rg, torch, pristine, buf, tmp, K, args.steps, args.warmup)
+                rows.append({"sms": k, "ms": ms, "records_per_s": n / (ms / 1e3)})
+        finally:
+            rg.set_plan(**old)
+        base = rows[0]
+        for r in rows:
+            r["speedup"] = base["ms"] / r["ms"]
+            r["efficiency"] = r["speedup"] / (r["sms"] / base["sms"])
+        value = rows[-1]["records_per_s"]
+        metric, unit = "records/s at all SMs", "records/s"
+    print(json.dumps({"metric": metric, "value": value, "unit": unit, "n_gpus": 1, "steps": args.steps,
+                      "warmup": args.warmup, "higher_is_better": args.workload != "tiny", "dtype": "u64",
+                      "data": "synthetic",
+                      "config": {"workload": args.workload, "keys": WORKLOADS[args.workload][5]},
+                      "peak_gbs": peak, "peak_source": peak_src, "rows": rows}), flush=True)
+    return 0
+
+
 def main():
     args = parse()
     if args.impl == "reference":
         return reference_arm(args)
+    if args.workload.startswith("sweep") or args.workload in ("tiny", "kmer_count"):
+        return sweeps(args)
     if args.workload.startswith("batched"):
         return batched(args)
     if args.workload.startswith("served"):

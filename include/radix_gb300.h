@@ -108,6 +108,21 @@ rs_status radix_histogram(const void *src, uint64_t n, uint32_t rec_size, uint32
                           uint32_t width, uint64_t *counts, rs_stream_t stream);
 
 /*
+ * Run-length count of equal keys in records that are already sorted by key: the counting
+ * step that follows the sort in k-mer counting (KMC3, the application of section 4).  A run
+ * is a maximal range of consecutive records with equal keys (key_size bytes).
+ *   in        DEVICE pointer to n sorted records (not modified); 16-byte aligned.
+ *   out       DEVICE pointer with room for n records: receives the first record of each run,
+ *             in order.
+ *   counts    DEVICE pointer with room for n uint64 values: counts[r] = records in run r.
+ *   d_nruns   DEVICE pointer to one uint64: the number of runs (0 for n = 0).
+ * Asynchronous on `stream`; uses a small part of the stream's library workspace (its
+ * status word is kept).  Records that are not sorted give runs of the unsorted sequence.
+ */
+rs_status radix_count_runs(const void *in, uint64_t n, uint32_t rec_size, uint32_t key_size, void *out,
+                           uint64_t *counts, uint64_t *d_nruns, rs_stream_t stream);
+
+/*
  * Waits for `stream` to drain, then reports (and clears) the device-side status of the
  * calls made on it: RS_OK, RS_ERR_DEVICE_TIMEOUT, RS_ERR_QUEUE_OVERFLOW, RS_ERR_INTERNAL
  * (a destination or range check failed; the offending writes were skipped), or RS_ERR_CUDA.

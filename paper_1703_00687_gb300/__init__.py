@@ -16,7 +16,7 @@ import ctypes
 
 from ._lib import KERNEL_NAMES, RadixSortError, RsKernelTime, RsPlan, check, lib
 
-__all__ = ["sort", "sort_host", "sort_segmented", "partition", "histogram", "status", "release", "set_plan",
+__all__ = ["sort", "sort_host", "sort_segmented", "partition", "histogram", "count_runs", "status", "release", "set_plan",
            "get_plan", "launch_count", "chunk_records", "workspace_bytes", "reserve",
            "profile", "RadixSortError", "lib", "SortGraph"]
 
@@ -131,6 +131,24 @@ def histogram(src, key_size: int, bit_lo: int, width: int, stream=None):
     check(lib().radix_histogram(src.data_ptr(), src.shape[0], _rec_size(src), key_size, bit_lo, width, out.data_ptr(),
                                 _stream(stream)), "radix_histogram")
     return out
+
+
+def count_runs(records, key_size: int, stream=None):
+    """Run-length count of equal keys in records already sorted by key (k-mer counting).
+
+    Returns (first, counts): the first record of every run (CUDA tensor, runs x rec_size
+    bytes) and the number of records in each run (CUDA int64 tensor).  Reads the number of
+    runs back to the host (synchronises the stream)."""
+    torch = _torch()
+    _need_cuda(records, "records")
+    n, R = records.shape[0], _rec_size(records)
+    out = torch.empty((max(n, 1), R), dtype=torch.uint8, device=records.device)
+    counts = torch.empty(max(n, 1), dtype=torch.int64, device=records.device)
+    nruns = torch.zeros(1, dtype=torch.int64, device=records.device)
+    check(lib().radix_count_runs(records.data_ptr(), n, R, key_size, out.data_ptr(), counts.data_ptr(),
+                                 nruns.data_ptr(), _stream(stream)), "radix_count_runs")
+    m = int(nruns.item())
+    return out[:m], counts[:m]
 
 
 def status(stream=None) -> int:

@@ -38,6 +38,7 @@ SIGNATURES = {
     "radix_sort_segmented": (_i32, [_vp, _vp, _vp, _u64, _u64, _u32, _u32, _vp]),
     "radix_partition": (_i32, [_vp, _vp, _u64, _u32, _u32, _u32, _u32, _vp]),
     "radix_histogram": (_i32, [_vp, _u64, _u32, _u32, _u32, _u32, _vp, _vp]),
+    "radix_count_runs": (_i32, [_vp, _u64, _u32, _u32, _vp, _vp, _vp, _vp]),
     "radix_sort_status": (_i32, [_vp]),
     "radix_sort_strerror": (ctypes.c_char_p, [_i32]),
     "radix_sort_release": (_i32, []),

@@ -20,6 +20,10 @@
 namespace rsg {
 
 u32 chunk_capacity(u32 RW);
+u64 runs_tiles(u64 n);
+u64 runs_bounds(u64 n);
+int launch_count_runs(const u64* recs, u64 n, u32 RW, u32 KW, u64 km0, u64 km1, u32* tile_cnt, u64* tile_off,
+                      u64* bound, u64* out, u64* counts, u64* nruns, u32 grid, cudaStream_t s);
 size_t level_smem_for(u32 T, u32 RW, u32 KW, u32 wmax);
 constexpr size_t kMaxSmemPerCta = 227 * 1024;
 
@@ -492,6 +496,42 @@ rs_status radix_histogram(const void* src, uint64_t n, uint32_t rec_size, uint32
                           uint32_t width, uint64_t* counts, rs_stream_t stream) {
   if (!counts) return RS_ERR_INVALID_ARG;
   return one_pass(src, nullptr, n, rec_size, key_size, bit_lo, width, counts, stream);
+}
+
+rs_status radix_count_runs(const void* in, uint64_t n, uint32_t rec_size, uint32_t key_size, void* out,
+                           uint64_t* counts, uint64_t* d_nruns, rs_stream_t stream) {
+  rs_status r = validate_layout(rec_size, key_size);
+  if (r != RS_OK) return r;
+  if (n > UINT64_MAX / rec_size) return RS_ERR_TOO_LARGE;
+  if (!d_nruns) return RS_ERR_INVALID_ARG;
+  cudaStream_t s = (cudaStream_t)stream;
+  if (check_device_ptr(d_nruns) != RS_OK) return RS_ERR_INVALID_ARG;
+  if (n == 0) return cudaMemsetAsync(d_nruns, 0, sizeof(uint64_t), s) == cudaSuccess ? RS_OK : RS_ERR_CUDA;
+  if (!in || !out || !counts) return RS_ERR_INVALID_ARG;
+  if ((((uintptr_t)in) | ((uintptr_t)out)) & 15) return RS_ERR_MISALIGNED;
+  if (overlap(in, out, n * rec_size)) return RS_ERR_OVERLAP;
+  if (check_device_ptr(in) != RS_OK || check_device_ptr(out) != RS_OK || check_device_ptr(counts) != RS_OK)
+    return RS_ERR_INVALID_ARG;
+  int dev = 0;
+  if (cudaGetDevice(&dev) != cudaSuccess) return RS_ERR_CUDA;
+  // tile counts, tile offsets and range bounds, after the workspace's control block
+  const u64 nt = runs_tiles(n), nbd = runs_bounds(n);
+  const size_t o_cnt = al(sizeof(Ctl)), o_off = al(o_cnt + nt * 4), o_bd = al(o_off + nt * 8), bytes = al(o_bd + nbd * 8);
+  Workspace* w = nullptr;
+  if ((r = get_workspace(dev, s, bytes, &w)) != RS_OK) return r;
+  char* base = (char*)w->mem;
+  const u32 KW = key_size > 8 ? 2 : 1;
+  u64 km[2];
+  for (u32 q = 0; q < 2; q++) {
+    const int b = (int)key_size - 8 * (int)q;
+    km[q] = b >= 8 ? ~0ull : b <= 0 ? 0ull : ((1ull << (8 * b)) - 1);
+  }
+  const u32 grid = (u32)sm_count(dev) * 8;
+  const int k = launch_count_runs((const u64*)in, n, rec_size / 8, KW, km[0], km[1], (u32*)(base + o_cnt),
+                                  (u64*)(base + o_off), (u64*)(base + o_bd), (u64*)out, (u64*)counts, (u64*)d_nruns, grid, s);
+  if (k < 0) return RS_ERR_CUDA;
+  count(k);
+  return RS_OK;
 }
 
 rs_status radix_sort_status(rs_stream_t stream) {

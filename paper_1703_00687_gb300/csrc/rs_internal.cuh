@@ -350,6 +350,33 @@ __device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commi
 // wait until at most one (the most recent) group of this thread's copies is still pending
 __device__ __forceinline__ void cp_async_wait_one() { asm volatile("cp.async.wait_group 1;\n" ::: "memory"); }
 
+// Exclusive prefix sum over the CTA of one value per thread (NT threads); ends with a barrier.
+template <int NT>
+__device__ __forceinline__ u32 block_exclusive_sum(u32 x, u32* scr) {
+  constexpr int kW = NT / 32;
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  u32 incl = x;
+#pragma unroll
+  for (int o = 1; o < 32; o <<= 1) {
+    const u32 y = __shfl_up_sync(kFull, incl, o);
+    if (lane >= o) incl += y;
+  }
+  if (lane == 31) scr[warp] = incl;
+  __syncthreads();
+  if (warp == 0) {
+    const u32 v = lane < kW ? scr[lane] : 0;
+    u32 t = v;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+      const u32 y = __shfl_up_sync(kFull, t, o);
+      if (lane >= o) t += y;
+    }
+    if (lane < kW) scr[lane] = t - v;
+  }
+  __syncthreads();
+  return scr[warp] + incl - x;
+}
+
 // Ask for [p, p + bytes) to be brought into L2 with one bulk request (the range shrunk to
 // 16-byte boundaries, so nothing outside it is touched).  Nothing waits for it.
 __device__ __forceinline__ void prefetch_l2(const void* p, u64 bytes) {

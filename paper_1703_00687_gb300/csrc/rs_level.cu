@@ -455,33 +455,6 @@ __device__ __forceinline__ u32 staged_digit(const u64* rec, u32 lo, u32 W) {
 // counters are read two at a time).
 __device__ __forceinline__ u32 digits_per_thread(u32 nd) { return nd > 2u * kSThreads ? nd / kSThreads : 2u; }
 
-// Exclusive prefix sum over the CTA of one value per thread (NT threads); ends with a barrier.
-template <int NT>
-__device__ __forceinline__ u32 block_exclusive_sum(u32 x, u32* scr) {
-  constexpr int kW = NT / 32;
-  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-  u32 incl = x;
-#pragma unroll
-  for (int o = 1; o < 32; o <<= 1) {
-    const u32 y = __shfl_up_sync(kFull, incl, o);
-    if (lane >= o) incl += y;
-  }
-  if (lane == 31) scr[warp] = incl;
-  __syncthreads();
-  if (warp == 0) {
-    const u32 v = lane < kW ? scr[lane] : 0;
-    u32 t = v;
-#pragma unroll
-    for (int o = 1; o < 32; o <<= 1) {
-      const u32 y = __shfl_up_sync(kFull, t, o);
-      if (lane >= o) t += y;
-    }
-    if (lane < kW) scr[lane] = t - v;
-  }
-  __syncthreads();
-  return scr[warp] + incl - x;
-}
-
 constexpr u64 kSkip = ~0ull;  // gbase of a digit whose run would leave its bin
 
 // Stable scatter of every large bin of the level into the other buffer.  The level's tiles

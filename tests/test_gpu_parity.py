@@ -64,7 +64,8 @@ LAYOUTS = [(8, 8), (8, 1), (8, 5), (16, 8), (16, 16), (24, 16), (32, 8), (40, 13
 @pytest.mark.parametrize("R,K", LAYOUTS)
 def test_sort_parity_sizes(R, K):
     rng = np.random.default_rng(R * 31 + K)
-    for n in (0, 1, 2, 3, 100, 4095, 4672, 4673, 9000, 70_001, 300_007):
+    cm = rg.chunk_records(R)  # the on-chip limit: sizes around it take different paths
+    for n in (0, 1, 2, 3, 100, 4095, cm, cm + 1, 9000, 70_001, 300_007):
         a = rand(rng, n, R, K)
         np.testing.assert_array_equal(gsort(a, K), oracle.sort(a, K), err_msg=f"n={n}")
 
@@ -167,3 +168,31 @@ def test_host_tensor_roundtrip():
     t = torch.from_numpy(a.copy())
     rg.sort(t, 8)
     np.testing.assert_array_equal(t.numpy(), oracle.sort(a, 8))
+
+
+# ------------------------------------------------ run-length counting after the sort (k-mer counting)
+@pytest.mark.parametrize("n,R,K,distinct", [(300_007, 24, 16, 5000), (200_000, 16, 8, 70_000), (9_000, 8, 3, 10),
+                                            (50_000, 24, 16, 1), (4097, 16, 8, None)])
+def test_count_runs_parity(n, R, K, distinct):
+    rng = np.random.default_rng(n + R)
+    a = rand(rng, n, R, K, distinct=distinct)
+    t = to_dev(a)
+    rg.sort(t, K)
+    first, counts = rg.count_runs(t, K)
+    torch.cuda.synchronize()
+    rg.check_status()
+    want_first, want_counts = oracle.count_runs(oracle.sort(a, K), K)
+    np.testing.assert_array_equal(from_dev(first), want_first)
+    np.testing.assert_array_equal(from_dev(counts).astype(np.uint64), want_counts)
+
+
+def test_count_runs_edge_cases():
+    for n in (0, 1):
+        t = torch.zeros((n, 16), dtype=torch.uint8, device="cuda")
+        first, counts = rg.count_runs(t, 8)
+        assert first.shape[0] == n and counts.tolist() == [1] * n
+    # one long run spanning many tiles, then single records
+    a = np.zeros((100_000, 8), dtype=np.uint8)
+    a[-3:, 0] = [1, 2, 3]
+    first, counts = rg.count_runs(to_dev(a), 8)
+    assert counts.tolist() == [99_997, 1, 1, 1]

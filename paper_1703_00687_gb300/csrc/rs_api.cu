@@ -12,6 +12,7 @@
 #include <map>
 #include <mutex>
 #include <utility>
+#include <algorithm>
 #include <vector>
 
 #include "radix_gb300.h"
@@ -137,9 +138,12 @@ static rs_status get_workspace(int dev, cudaStream_t s, size_t bytes, Workspace*
   return RS_OK;
 }
 
-// Tile ranges of a level: one per histogram CTA that fits on the GPU at once.
+// Tile ranges of a level: as many as histogram or scatter CTAs fit on the GPU at once,
+// whichever is more (every scatter CTA needs a lane of its own; histogram CTAs beyond the
+// resident ones simply run in a second wave).
 static u32 lanes_for(const Job& j, int sms) {
-  const u64 l = (u64)sms * (u64)hist_ctas_per_sm(j);
+  const int per_sm = std::max(hist_ctas_per_sm(j), scatter_ctas_per_sm(j));
+  const u64 l = (u64)sms * (u64)per_sm;
   return (u32)(l < 1 ? 1 : l > kMaxLanes ? kMaxLanes : l);
 }
 

@@ -132,10 +132,17 @@ struct DigitSpec {
   }
 };
 
-// Window of kWinBits bits right below bit p (all bits >= p shared), no sub-bin number.
-__device__ __forceinline__ DigitSpec window_below(u32 p) {
+// Window right below bit p (all bits >= p shared), no sub-bin number: kWinBits bits, or
+// fewer for a range of s records (about 2 to 4 buckets per record: the counters to scan
+// then scale with the range).
+__device__ __forceinline__ DigitSpec window_below(u32 p, u32 s = 1u << kIdxBits) {
+  u32 w = kWinBits;
+  if (s < (1u << (kWinBits - 2))) {
+    w = 4;
+    while ((1u << (w - 2)) < s) w++;
+  }
   DigitSpec d = {};
-  d.w = p > (u32)kWinBits ? (u32)kWinBits : p;
+  d.w = p > w ? w : p;
   d.lo = p - d.w;
   return d;
 }
@@ -264,6 +271,23 @@ __device__ u32 range_top_bit(const ChunkCtx<KW, RWT>& c, u32 a, u32 s, bool thro
   return p;
 }
 
+// A chunk of at most kEsMax records: enumeration sort of the whole range at once (each
+// record's rank among all of them by (key, input position)); the counters stay untouched.
+// Kept out of line so that it does not disturb the code of the common path.
+template <int KW, int RWT>
+__device__ __noinline__ void small_chunk_sort(const ChunkCtx<KW, RWT>& c, u32 sz) {
+  for (u32 i = threadIdx.x; i < sz; i += kCThreads) {
+    const Key<KW> kr = c.key(i);
+    u32 rank = 0;
+    for (u32 q = 0; q < sz; q++) {
+      const Key<KW> k2 = c.key(q);
+      rank += key_less<KW>(k2, kr) || (key_eq<KW>(k2, kr) && q < i);
+    }
+    c.perm[rank] = (u16)i;
+  }
+  __syncthreads();
+}
+
 // Persistent CTAs take chunks by ticket.  With two stage buffers the next chunk's records
 // stream in while the current chunk is sorted; with one, the CTAs sharing an SM overlap.
 template <int KW, int RWT>
@@ -311,10 +335,21 @@ __global__ void __launch_bounds__(kCThreads, kChunkCtas) k_chunk(Job j) {
     cp_async_commit();
   };
 
+  // Tickets are dispensed in batches when chunks are many (many tiny segments): thread 0
+  // owns tickets [t_next, t_end) and takes the next batch with one atomic.
+  const u64 batch = nch >= (u64)gridDim.x * 2048 ? 8 : 1;
+  u64 t_next = 0, t_end = 0;
+  auto take = [&]() -> u64 {
+    if (t_next == t_end) {
+      t_next = atomicAdd(&ctl->chunk_ticket, batch);
+      t_end = t_next + batch;
+    }
+    return t_next++;
+  };
   for (u32 i = tid; i < (u32)kCntWords; i += kCThreads) c.cnt[i] = 0;
   if (tid == 0) {
-    fetch(0, atomicAdd(&ctl->chunk_ticket, 1ull));
-    if (kChunkStages == 2) fetch(1, atomicAdd(&ctl->chunk_ticket, 1ull));
+    fetch(0, take());
+    if (kChunkStages == 2) fetch(1, take());
   }
   __syncthreads();
   if (kChunkStages == 2) {
@@ -327,11 +362,11 @@ __global__ void __launch_bounds__(kCThreads, kChunkCtas) k_chunk(Job j) {
       cp_async_wait_one();
       __syncthreads();
     }
-    if (s_t[cur] >= nch) break;  // tickets are taken in order: no later chunk either
+    if (s_t[cur] >= nch) break;  // a CTA's tickets only grow: no later chunk either
     const Chunk ch = s_ch[cur];
     if (kChunkStages == 1) issue(cur);
     u64 nt = 0;
-    if (tid == 0) nt = atomicAdd(&ctl->chunk_ticket, 1ull);  // described during this chunk
+    if (tid == 0) nt = take();  // described during this chunk
     if (kChunkStages == 1) {
       cp_async_wait_all();
       __syncthreads();
@@ -345,7 +380,7 @@ __global__ void __launch_bounds__(kCThreads, kChunkCtas) k_chunk(Job j) {
     bool sort = sz && !(ch.flags & kChCopyOnly);
     if (sort) {
       if (ch.p) {  // shared bits known from the level that produced the chunk
-        dig = window_below(ch.p);
+        dig = window_below(ch.p, sz);
         if (ch.sb) {
           dig.sb = ch.sb;
           dig.plo = ch.p;
@@ -357,16 +392,18 @@ __global__ void __launch_bounds__(kCThreads, kChunkCtas) k_chunk(Job j) {
       } else {
         const u32 p = range_top_bit(c, 0, sz, false);  // (ends with a barrier)
         sort = p != 0;
-        dig = window_below(p);
+        dig = window_below(p, sz);
       }
     }
-    if (sort) {
+    if (sort && sz > (u32)kEsMax) {
       if (tid == 0) s_top = 0;
       // s_ch[cur] has been read by every thread (a barrier lies inside sort_round before
       // thread 0 rewrites it below)
       sort_round(c, 0, sz, dig, &s_top, true, true);
       if (tid == 0) fetch(cur, nt);
+      u32 used = ((1u << dig.bits()) + 1) >> 1;  // counter words the rounds have touched
       while (s_top) {  // s_top is final after the barrier that ends every round
+        used = kCntWords;
         const u32 top = s_top;
         if (top > c.stack_cap) {  // cannot happen: buckets on the stack are disjoint and > kEsMax
           if (tid == 0) atomicOr(&ctl->err, kErrInternal);
@@ -386,7 +423,12 @@ __global__ void __launch_bounds__(kCThreads, kChunkCtas) k_chunk(Job j) {
         }
       }
       // counters back to zero for the next chunk's first distribution
-      for (u32 i = tid; i < (u32)kCntWords; i += kCThreads) c.cnt[i] = 0;
+      for (u32 i = tid; i < used; i += kCThreads) c.cnt[i] = 0;
+    } else if (sort) {
+      small_chunk_sort(c, sz);  // (ends with a barrier: every thread has read s_ch[cur])
+      if (tid == 0) fetch(cur, nt);
+    }
+    if (sort) {
       // write the records in sorted order
       if (RW == 2) {
         for (u32 s = tid; s < sz; s += kCThreads) {

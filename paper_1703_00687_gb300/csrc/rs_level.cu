@@ -111,44 +111,62 @@ __global__ void k_reset(Job j) {
   }
 }
 
-// Segmented (batched) start: every segment is a level-0 bin (if large) or a chunk.
+// Segmented (batched) start: every segment is a level-0 bin (if large) or a chunk.  Chunk
+// slots are reserved with one atomic per warp (batches hold up to millions of small segments).
 __global__ void __launch_bounds__(kThreads) k_init_segments(Job j) {
   Ctl* ctl = j.ctl;
-  for (u64 s = blockIdx.x * (u64)kThreads + threadIdx.x; s < j.n_segs; s += (u64)gridDim.x * kThreads) {
-    const u64 a = j.seg_off[s], e = j.seg_off[s + 1];
-    if (e < a || e > j.n) {  // offsets not non-decreasing within [0, total]: skip, report
-      atomicOr(&ctl->err, kErrInternal);
-      continue;
+  const u32 lane = threadIdx.x & 31;
+  for (u64 base = blockIdx.x * (u64)kThreads; base < j.n_segs; base += (u64)gridDim.x * kThreads) {
+    const u64 s = base + threadIdx.x;
+    u64 a = 0, c = 0;
+    bool to_chunk = false, to_bin = false;
+    if (s < j.n_segs) {
+      const u64 e = j.seg_off[s + 1];
+      a = j.seg_off[s];
+      if (e < a || e > j.n) {  // offsets not non-decreasing within [0, total]: skip, report
+        atomicOr(&ctl->err, kErrInternal);
+      } else if (e > a + 1) {
+        c = e - a;
+        to_chunk = c <= j.chunk_max;
+        to_bin = !to_chunk;
+      }
     }
-    if (e <= a + 1) continue;
-    const u64 c = e - a;
-    if (c <= j.chunk_max) {
-      const u64 idx = atomicAdd(&ctl->nchunks, 1ull);
-      if (idx >= j.cap_chunks) { atomicOr(&ctl->err, kErrOverflow); continue; }
-      Chunk ch = {};
-      ch.begin = a;
-      ch.size = (u32)c;
-      j.chunks[idx] = ch;
-      continue;
+    const u32 want = __ballot_sync(kFull, to_chunk);
+    u64 first = 0;
+    if (want) {
+      const int leader = __ffs(want) - 1;
+      if ((int)lane == leader) first = atomicAdd(&ctl->nchunks, (u64)__popc(want));
+      first = __shfl_sync(kFull, first, leader);
     }
+    if (to_chunk) {
+      const u64 idx = first + __popc(want & lanemask_lt());
+      if (idx >= j.cap_chunks) {
+        atomicOr(&ctl->err, kErrOverflow);
+      } else {
+        Chunk ch = {};
+        ch.begin = a;
+        ch.size = (u32)c;
+        j.chunks[idx] = ch;
+      }
+    }
+    if (!to_bin) continue;
     u32 lo, W;
     plan_digit(c, 8 * j.K, j.chunk_max, j.wmax, &lo, &W);
     const u32 nd = 1u << W;
-    const u64 tiles = ceil_div(c, j.T);
     const u64 idx = atomicAdd(&ctl->nbins[0], 1ull);
     const u64 bo = atomicAdd(&ctl->base_used[0], (u64)nd);
     if (idx >= j.cap_bins || bo + nd > j.cap_base) {
       atomicOr(&ctl->err, kErrOverflow);
       continue;
     }
-    Bin b = {};
-    b.begin = a;
-    b.size = c;
-    b.base_off = bo;
-    b.kand[0] = b.kand[1] = ~0ull;
-    b.lo = lo;
-    b.W = W;
-    j.bins[0][idx] = b;
+    Bin bn = {};
+    bn.begin = a;
+    bn.size = c;
+    bn.base_off = bo;
+    bn.kand[0] = bn.kand[1] = ~0ull;
+    bn.lo = lo;
+    bn.W = W;
+    j.bins[0][idx] = bn;
     for (u32 v = 0; v < nd; v++) j.base[0][bo + v] = 0;
   }
 }

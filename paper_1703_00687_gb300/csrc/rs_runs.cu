@@ -13,8 +13,10 @@
 namespace rsg {
 
 constexpr int kRThreads = 256;
-constexpr u32 kRItems = 16;                    // consecutive records per thread
-constexpr u32 kRTile = kRThreads * kRItems;    // records per tile
+constexpr int kRWarps = kRThreads / 32;
+constexpr u32 kRRange = 4096;                  // runs per range of k_runs_len
+constexpr u32 kRItems = 16;                    // rounds of 32 records per warp and tile
+constexpr u32 kRTile = kRThreads * kRItems;    // records per tile (warp w: records [w*512, w*512+512))
 
 template <int KW>
 __device__ __forceinline__ Key<KW> run_key(const u64* recs, u64 i, u32 RW, u64 km0, u64 km1) {
@@ -24,41 +26,51 @@ __device__ __forceinline__ Key<KW> run_key(const u64* recs, u64 i, u32 RW, u64 k
   return k;
 }
 
-// Number of records in [i0, i1) that start a run.
+// One round of a warp over records [r, r + 32) (lane l: record r + l, coalesced): which lanes
+// start a run.  prev = key of record r - 1 (any value when r == 0), passed round to round.
 template <int KW>
-__device__ __forceinline__ u32 run_starts_in(const u64* recs, u64 i0, u64 i1, u32 RW, u64 km0, u64 km1) {
-  if (i0 >= i1) return 0;
-  u32 c = 0;
-  Key<KW> prev = i0 ? run_key<KW>(recs, i0 - 1, RW, km0, km1) : Key<KW>{};
-  for (u64 i = i0; i < i1; i++) {
-    const Key<KW> k = run_key<KW>(recs, i, RW, km0, km1);
-    c += (i == 0 || !key_eq<KW>(k, prev)) ? 1u : 0u;
-    prev = k;
+__device__ __forceinline__ u32 run_start_mask(const u64* recs, u64 n, u64 r, u32 RW, u64 km0, u64 km1,
+                                              Key<KW>& prev) {
+  const u32 lane = threadIdx.x & 31;
+  const u64 i = r + lane;
+  Key<KW> k = prev;
+  if (i < n) k = run_key<KW>(recs, i, RW, km0, km1);
+  Key<KW> before;
+#pragma unroll
+  for (int q = 0; q < KW; q++) {
+    before.w[q] = __shfl_up_sync(kFull, k.w[q], 1);
+    if (lane == 0) before.w[q] = prev.w[q];
+    prev.w[q] = __shfl_sync(kFull, k.w[q], 31);
   }
-  return c;
+  return __ballot_sync(kFull, i < n && (i == 0 || !key_eq<KW>(k, before)));
 }
 
-__device__ __forceinline__ u32 block_sum_u32(u32 x, u32* scr) {
-  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-  x = __reduce_add_sync(kFull, x);
-  if (lane == 0) scr[warp] = x;
-  __syncthreads();
-  u32 t = 0;
-  if (threadIdx.x == 0)
-    for (int w = 0; w < kRThreads / 32; w++) t += scr[w];
-  __syncthreads();
-  return t;  // valid in thread 0
+// Runs starting in the warp's part of a tile (records [r0, r0 + 32 * kRItems)).
+template <int KW>
+__device__ __forceinline__ u32 warp_run_starts(const u64* recs, u64 n, u64 r0, u32 RW, u64 km0, u64 km1) {
+  Key<KW> prev = {};
+  if (r0 > 0 && r0 - 1 < n) prev = run_key<KW>(recs, r0 - 1, RW, km0, km1);
+  u32 c = 0;
+  for (u32 it = 0; it < kRItems; it++) c += __popc(run_start_mask<KW>(recs, n, r0 + 32 * it, RW, km0, km1, prev));
+  return c;
 }
 
 template <int KW>
 __global__ void __launch_bounds__(kRThreads) k_runs_tiles(const u64* recs, u64 n, u32 RW, u64 km0, u64 km1,
                                                           u32* tile_cnt, u64 ntiles) {
-  __shared__ u32 scr[kRThreads / 32];
+  __shared__ u32 scr[kRWarps];
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   for (u64 tile = blockIdx.x; tile < ntiles; tile += gridDim.x) {
-    const u64 i0 = tile * kRTile + (u64)threadIdx.x * kRItems;
-    const u32 c = run_starts_in<KW>(recs, min(i0, n), min(i0 + kRItems, n), RW, km0, km1);
-    const u32 t = block_sum_u32(c, scr);
-    if (threadIdx.x == 0) tile_cnt[tile] = t;
+    const u64 r0 = tile * kRTile + (u64)warp * 32 * kRItems;
+    const u32 c = warp_run_starts<KW>(recs, n, r0, RW, km0, km1);
+    if (lane == 0) scr[warp] = c;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+      u32 t = 0;
+      for (int w = 0; w < kRWarps; w++) t += scr[w];
+      tile_cnt[tile] = t;
+    }
+    __syncthreads();
   }
 }
 
@@ -97,7 +109,6 @@ __global__ void __launch_bounds__(1024) k_runs_scan(const u32* tile_cnt, u64 nti
   if (threadIdx.x == 0) *nruns = carry;
 }
 
-constexpr u32 kRRange = 4096;  // runs per range of k_runs_len
 
 // Per tile: the first record of every run that starts in it goes to out[run]; counts[run]
 // receives the index of that record (turned into lengths by k_runs_len), and the start of
@@ -106,26 +117,32 @@ template <int KW>
 __global__ void __launch_bounds__(kRThreads) k_runs_write(const u64* recs, u64 n, u32 RW, u64 km0, u64 km1,
                                                           const u64* tile_off, u64 ntiles, u64* out, u64* counts,
                                                           u64* bound) {
-  __shared__ u32 scr[kRThreads / 32 + 1];
-  const int tid = threadIdx.x;
+  __shared__ u32 scr[kRWarps];
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const u32 ltmask = lanemask_lt();
   for (u64 tile = blockIdx.x; tile < ntiles; tile += gridDim.x) {
-    const u64 i0 = min(n, tile * kRTile + (u64)tid * kRItems), i1 = min(n, i0 + kRItems);
-    const u32 mine = run_starts_in<KW>(recs, i0, i1, RW, km0, km1);
-    u64 p = tile_off[tile] + block_exclusive_sum<kRThreads>(mine, scr);  // next run to start
-    if (mine) {
-      Key<KW> prev = i0 ? run_key<KW>(recs, i0 - 1, RW, km0, km1) : Key<KW>{};
-      for (u64 i = i0; i < i1; i++) {
-        const Key<KW> k = run_key<KW>(recs, i, RW, km0, km1);
-        if (i == 0 || !key_eq<KW>(k, prev)) {
-          for (u32 w = 0; w < RW; w++) out[p * RW + w] = recs[i * RW + w];
-          counts[p] = i;
-          if (p % kRRange == 0) bound[p / kRRange] = i;
-          p++;
-        }
-        prev = k;
+    const u64 r0 = tile * kRTile + (u64)warp * 32 * kRItems;
+    // runs starting in the warps before this one, then this warp's rounds in order
+    const u32 mine = warp_run_starts<KW>(recs, n, r0, RW, km0, km1);
+    if (lane == 0) scr[warp] = mine;
+    __syncthreads();
+    u64 p = tile_off[tile];
+    for (int w = 0; w < warp; w++) p += scr[w];
+    __syncthreads();  // scr is reused by the next tile
+    if (mine == 0) continue;
+    Key<KW> prev = {};
+    if (r0 > 0 && r0 - 1 < n) prev = run_key<KW>(recs, r0 - 1, RW, km0, km1);
+    for (u32 it = 0; it < kRItems; it++) {
+      const u64 r = r0 + 32 * it;
+      const u32 m = run_start_mask<KW>(recs, n, r, RW, km0, km1, prev);
+      if (m >> lane & 1u) {
+        const u64 q = p + __popc(m & ltmask), i = r + lane;
+        for (u32 w = 0; w < RW; w++) out[q * RW + w] = recs[i * RW + w];
+        counts[q] = i;
+        if (q % kRRange == 0) bound[q / kRRange] = i;
       }
+      p += __popc(m);
     }
-    __syncthreads();  // the scan scratch is reused by the next tile
   }
 }
 

@@ -401,9 +401,7 @@ __global__ void __launch_bounds__(kCThreads, kChunkCtas) k_chunk(Job j) {
       // thread 0 rewrites it below)
       sort_round(c, 0, sz, dig, &s_top, true, true);
       if (tid == 0) fetch(cur, nt);
-      u32 used = ((1u << dig.bits()) + 1) >> 1;  // counter words the rounds have touched
       while (s_top) {  // s_top is final after the barrier that ends every round
-        used = kCntWords;
         const u32 top = s_top;
         if (top > c.stack_cap) {  // cannot happen: buckets on the stack are disjoint and > kEsMax
           if (tid == 0) atomicOr(&ctl->err, kErrInternal);
@@ -416,14 +414,24 @@ __global__ void __launch_bounds__(kCThreads, kChunkCtas) k_chunk(Job j) {
         const u32 pp = range_top_bit(c, a, s, true);
         if (pp) {
           sort_round(c, a, s, window_below(pp), &s_top);
-        } else {  // all keys equal: back to input order
+        } else if (s <= 4 * kEsMax) {  // all keys equal: back to input order, by rank
+          for (u32 i = tid; i < s; i += kCThreads) {
+            const u32 r = c.perm[a + i];
+            u32 rank = 0;
+            for (u32 q = 0; q < s; q++) rank += c.perm[a + q] < r;
+            c.out[a + rank] = (u16)r;
+          }
+          __syncthreads();
+          for (u32 i = tid; i < s; i += kCThreads) c.perm[a + i] = c.out[a + i];
+          __syncthreads();
+        } else {  // all keys equal: back to input order by one counting pass on the positions
           distribute(c, a, s, true, DigitSpec{}, false, false);
           for (u32 i = tid; i < s; i += kCThreads) c.perm[a + i] = c.out[a + i];
           __syncthreads();
         }
       }
       // counters back to zero for the next chunk's first distribution
-      for (u32 i = tid; i < used; i += kCThreads) c.cnt[i] = 0;
+      for (u32 i = tid; i < (u32)kCntWords; i += kCThreads) c.cnt[i] = 0;
     } else if (sort) {
       small_chunk_sort(c, sz);  // (ends with a barrier: every thread has read s_ch[cur])
       if (tid == 0) fetch(cur, nt);

@@ -271,6 +271,38 @@ __device__ u32 range_top_bit(const ChunkCtx<KW, RWT>& c, u32 a, u32 s, bool thro
   return p;
 }
 
+// Positions [a, a + s) of c.perm hold records with equal keys in some order: put them back in
+// input order (increasing record index).  A bitmap of the chunk's record indices (borrowing
+// the counters, which are cleared before their next use) marks the bucket's records; a
+// record's new place is the number of marked indices below its own.  Ends with a barrier.
+template <int KW, int RWT>
+__device__ void restore_input_order(const ChunkCtx<KW, RWT>& c, u32 a, u32 s) {
+  __shared__ u32 scr[kCWarps];
+  constexpr u32 kWords = (1u << kIdxBits) / 32;  // bitmap words over every possible index
+  static_assert(kWords <= (u32)kCThreads, "one bitmap word per thread");
+  u32* bm = c.cnt;             // [kWords] the bitmap
+  u32* below = c.cnt + kWords;  // [kWords] marked indices in the words before
+  const u32 tid = threadIdx.x;
+  for (u32 w = tid; w < kWords; w += kCThreads) bm[w] = 0;
+  __syncthreads();
+  for (u32 i = tid; i < s; i += kCThreads) {
+    const u32 r = c.perm[a + i];
+    atomicOr(&bm[r >> 5], 1u << (r & 31));
+  }
+  __syncthreads();
+  const u32 mine = tid < kWords ? bm[tid] : 0u;
+  const u32 ex = block_exclusive_sum<kCThreads>(__popc(mine), scr);  // ends with a barrier
+  if (tid < kWords) below[tid] = ex;
+  __syncthreads();
+  for (u32 i = tid; i < s; i += kCThreads) {
+    const u32 r = c.perm[a + i];
+    c.out[a + below[r >> 5] + __popc(bm[r >> 5] & ((1u << (r & 31)) - 1u))] = (u16)r;
+  }
+  __syncthreads();
+  for (u32 i = tid; i < s; i += kCThreads) c.perm[a + i] = c.out[a + i];
+  __syncthreads();
+}
+
 // A chunk of at most kEsMax records: enumeration sort of the whole range at once (each
 // record's rank among all of them by (key, input position)); the counters stay untouched.
 // Kept out of line so that it does not disturb the code of the common path.
@@ -414,20 +446,8 @@ __global__ void __launch_bounds__(kCThreads, kChunkCtas) k_chunk(Job j) {
         const u32 pp = range_top_bit(c, a, s, true);
         if (pp) {
           sort_round(c, a, s, window_below(pp), &s_top);
-        } else if (s <= 4 * kEsMax) {  // all keys equal: back to input order, by rank
-          for (u32 i = tid; i < s; i += kCThreads) {
-            const u32 r = c.perm[a + i];
-            u32 rank = 0;
-            for (u32 q = 0; q < s; q++) rank += c.perm[a + q] < r;
-            c.out[a + rank] = (u16)r;
-          }
-          __syncthreads();
-          for (u32 i = tid; i < s; i += kCThreads) c.perm[a + i] = c.out[a + i];
-          __syncthreads();
-        } else {  // all keys equal: back to input order by one counting pass on the positions
-          distribute(c, a, s, true, DigitSpec{}, false, false);
-          for (u32 i = tid; i < s; i += kCThreads) c.perm[a + i] = c.out[a + i];
-          __syncthreads();
+        } else {  // all keys equal: back to input order
+          restore_input_order(c, a, s);
         }
       }
       // counters back to zero for the next chunk's first distribution

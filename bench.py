@@ -86,9 +86,17 @@ def measured_peaks():
         return 6800.0, "fallback"
 
 
-def kernel_source_sha():
+KERNEL_SOURCES = {"scatter": ["rs_level.cu", "rs_internal.cuh"], "hist": ["rs_level.cu", "rs_internal.cuh"],
+                  "chunk": ["rs_chunk.cu", "rs_internal.cuh"]}
+
+
+def kernel_source_sha(kernel=None):
+    """Hash of the sources a kernel is built from (all kernel sources when none is named)."""
+    csrc = os.path.join(ROOT, "paper_1703_00687_gb300", "csrc")
+    files = [os.path.join(csrc, f) for f in KERNEL_SOURCES[kernel]] if kernel in KERNEL_SOURCES else \
+        sorted(glob.glob(os.path.join(csrc, "*")))
     h = hashlib.sha256()
-    for p in sorted(glob.glob(os.path.join(ROOT, "paper_1703_00687_gb300", "csrc", "*"))):
+    for p in files:
         with open(p, "rb") as f:
             h.update(f.read())
     return h.hexdigest()[:16]
@@ -101,7 +109,7 @@ def committed_traffic(kernel, workload):
         with open(path) as f:
             d = json.load(f)
         e = d[kernel]
-        if e.get("source_sha") != kernel_source_sha():
+        if e.get("source_sha") != kernel_source_sha(kernel):
             return None
         return float(e["dram_bytes_per_full_launch"]) if e.get("workload") == workload else None
     except Exception:

@@ -234,7 +234,9 @@ def test_planted_mistakes_fail_a_pin(name):
     old, new = MUTANTS[name]
     src = open(os.path.join(os.path.dirname(oracle.__file__), "oracle.c")).read()
     assert src.count(old) == 1, name
-    with tempfile.TemporaryDirectory() as d:
+    build_dir = os.path.join(os.path.dirname(oracle.__file__), "_build")
+    os.makedirs(build_dir, exist_ok=True)
+    with tempfile.TemporaryDirectory(dir=build_dir) as d:  # (inside the repository)
         path = os.path.join(d, name + ".c")
         open(path, "w").write(src.replace(old, new))
         so = os.path.join(d, name + ".so")

@@ -7,13 +7,14 @@
 //
 // The index sort follows the paper's small/tiny-bin scheme on chip:
 //   * skip the key bits every record of the range shares (AND/OR of the keys);
-//   * one counting-sort distribution on the next kWinBits bits, with shared-memory atomic
-//     counters (the order inside a bucket is arbitrary here);
+//   * one counting-sort distribution on the next kWinBits bits (fewer for a small chunk),
+//     with shared-memory atomic counters (the order inside a bucket is arbitrary here);
 //   * every bucket of up to kEsMax records is finished by enumeration sort (section 2.2,
 //     3.3): a record's place is the number of records of the bucket that must precede it,
 //     comparing (key, input position) -- so equal keys come out in input order;
 //   * a larger bucket is processed again the same way; if all its keys are equal it is put
-//     back in input order by one counting pass on the (unique) input positions.
+//     back in input order (ranks of its input positions, from a bitmap of them);
+//   * a chunk of at most kEsMax records is one enumeration sort, without a distribution.
 // The result is therefore the stable order, and the whole sorter is stable.
 #include "rs_internal.cuh"
 
@@ -149,13 +150,12 @@ __device__ __forceinline__ DigitSpec window_below(u32 p, u32 s = 1u << kIdxBits)
 
 // Distributes positions [a, a + s) of c.perm into c.out by a digit of the record (any order
 // inside a bucket); afterwards c.cnt holds every bucket's first position (relative to a).
-// by_index: the digit is the record's input position (unique); else dig.
 // identity: c.perm is the identity over the range (not read).  zeroed: c.cnt is already 0.
 template <int KW, int RWT>
-__device__ void distribute(const ChunkCtx<KW, RWT>& c, u32 a, u32 s, bool by_index, const DigitSpec& dig,
+__device__ void distribute(const ChunkCtx<KW, RWT>& c, u32 a, u32 s, const DigitSpec& dig,
                            bool identity, bool zeroed) {
   const int tid = threadIdx.x;
-  const u32 nd = by_index ? (1u << kIdxBits) : (1u << dig.bits());
+  const u32 nd = 1u << dig.bits();
   const u32 words = (nd + 1) >> 1;
   if (!zeroed) {
     for (u32 i = tid; i < words; i += kCThreads) c.cnt[i] = 0;
@@ -168,7 +168,7 @@ __device__ void distribute(const ChunkCtx<KW, RWT>& c, u32 a, u32 s, bool by_ind
     held[k] = 0xffffffffu;
     if (i < s) {
       const u32 r = identity ? a + i : c.perm[a + i];
-      const u32 d = by_index ? r : dig.of<KW>(c.key(r));
+      const u32 d = dig.of<KW>(c.key(r));
       const u32 old = atomicAdd(&c.cnt[d >> 1], 1u << ((d & 1) * 16));
       held[k] = (((old >> ((d & 1) * 16)) & 0xffffu)) | (d << 16);
     }
@@ -194,7 +194,7 @@ __device__ void sort_round(const ChunkCtx<KW, RWT>& c, u32 a, u32 s, const Digit
                            bool identity = false, bool zeroed = false) {
   const int tid = threadIdx.x;
   const u32 nd = 1u << dig.bits();
-  distribute(c, a, s, false, dig, identity, zeroed);
+  distribute(c, a, s, dig, identity, zeroed);
   for (u32 i = tid; i < s; i += kCThreads) {
     const u32 r = c.out[a + i];
     const Key<KW> kr = c.key(r);

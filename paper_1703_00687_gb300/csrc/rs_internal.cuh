@@ -207,124 +207,6 @@ __device__ __forceinline__ u32 lanemask_lt() {
   return m;
 }
 
-__device__ __forceinline__ u32 ld_acquire(const u32* p) {
-  u32 v;
-  asm volatile("ld.acquire.gpu.global.u32 %0, [%1];" : "=r"(v) : "l"(p) : "memory");
-  return v;
-}
-__device__ __forceinline__ u64 ld_acquire(const u64* p) {
-  u64 v;
-  asm volatile("ld.acquire.gpu.global.u64 %0, [%1];" : "=l"(v) : "l"(p) : "memory");
-  return v;
-}
-__device__ __forceinline__ void st_release(u32* p, u32 v) {
-  asm volatile("st.release.gpu.global.u32 [%0], %1;" ::"l"(p), "r"(v) : "memory");
-}
-__device__ __forceinline__ void st_release(u64* p, u64 v) {
-  asm volatile("st.release.gpu.global.u64 [%0], %1;" ::"l"(p), "l"(v) : "memory");
-}
-// Relaxed (unfenced) device-scope accesses: for words that carry their own payload, such as
-// the look-back words (a state and a count in one word), no ordering with other data is needed.
-__device__ __forceinline__ u32 ld_relaxed(const u32* p) {
-  u32 v;
-  asm volatile("ld.relaxed.gpu.global.u32 %0, [%1];" : "=r"(v) : "l"(p) : "memory");
-  return v;
-}
-__device__ __forceinline__ u64 ld_relaxed(const u64* p) {
-  u64 v;
-  asm volatile("ld.relaxed.gpu.global.u64 %0, [%1];" : "=l"(v) : "l"(p) : "memory");
-  return v;
-}
-__device__ __forceinline__ void st_relaxed(u32* p, u32 v) {
-  asm volatile("st.relaxed.gpu.global.u32 [%0], %1;" ::"l"(p), "r"(v) : "memory");
-}
-__device__ __forceinline__ void st_relaxed(u64* p, u64 v) {
-  asm volatile("st.relaxed.gpu.global.u64 [%0], %1;" ::"l"(p), "l"(v) : "memory");
-}
-
-// Exclusive scan of n u32 values in shared memory, in place, by a CTA of NT threads; returns
-// the total.  All threads of the CTA must call it.  `scratch` holds NT/32 + 1 u32.
-template <int NT = kThreads>
-__device__ inline u32 block_exclusive_scan(u32* a, int n, u32* scratch) {
-  constexpr int kW = NT / 32;
-  const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
-  const int per = (n + NT - 1) / NT;
-  const int b = tid * per;
-  u32 sum = 0;
-  for (int i = 0; i < per; i++)
-    if (b + i < n) sum += a[b + i];
-  u32 x = sum;
-#pragma unroll
-  for (int o = 1; o < 32; o <<= 1) {
-    u32 y = __shfl_up_sync(kFull, x, o);
-    if (lane >= o) x += y;
-  }
-  if (lane == 31) scratch[warp] = x;
-  __syncthreads();
-  if (warp == 0) {
-    u32 w = lane < kW ? scratch[lane] : 0;
-    u32 s = w;
-#pragma unroll
-    for (int o = 1; o < 32; o <<= 1) {
-      u32 y = __shfl_up_sync(kFull, s, o);
-      if (lane >= o) s += y;
-    }
-    if (lane < kW) scratch[lane] = s - w;
-    if (lane == kW - 1) scratch[kW] = s;
-  }
-  __syncthreads();
-  u32 run = scratch[warp] + x - sum;
-  for (int i = 0; i < per; i++)
-    if (b + i < n) {
-      u32 v = a[b + i];
-      a[b + i] = run;
-      run += v;
-    }
-  u32 total = scratch[kW];
-  __syncthreads();
-  return total;
-}
-
-// Same for u64 values.
-__device__ inline u64 block_exclusive_scan64(u64* a, int n, u64* scratch) {
-  const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
-  const int per = (n + kThreads - 1) / kThreads;
-  const int b = tid * per;
-  u64 sum = 0;
-  for (int i = 0; i < per; i++)
-    if (b + i < n) sum += a[b + i];
-  u64 x = sum;
-#pragma unroll
-  for (int o = 1; o < 32; o <<= 1) {
-    u64 y = __shfl_up_sync(kFull, x, o);
-    if (lane >= o) x += y;
-  }
-  if (lane == 31) scratch[warp] = x;
-  __syncthreads();
-  if (warp == 0) {
-    u64 w = lane < kWarps ? scratch[lane] : 0;
-    u64 s = w;
-#pragma unroll
-    for (int o = 1; o < 32; o <<= 1) {
-      u64 y = __shfl_up_sync(kFull, s, o);
-      if (lane >= o) s += y;
-    }
-    if (lane < kWarps) scratch[lane] = s - w;
-    if (lane == kWarps - 1) scratch[kWarps] = s;
-  }
-  __syncthreads();
-  u64 run = scratch[warp] + x - sum;
-  for (int i = 0; i < per; i++)
-    if (b + i < n) {
-      u64 v = a[b + i];
-      a[b + i] = run;
-      run += v;
-    }
-  u64 total = scratch[kWarps];
-  __syncthreads();
-  return total;
-}
-
 // Bin of a tile: the last bin whose tile_start <= t (bins are in tile order).
 __device__ __forceinline__ u64 find_bin(const Bin* bins, u64 nb, u64 t) {
   u64 lo = 0, hi = nb;  // invariant: bins[lo].tile_start <= t < bins[hi].tile_start
@@ -400,34 +282,6 @@ __device__ __forceinline__ void load_words_async(u64* dst, const u64* src, u64 w
   }
 }
 
-// Copy `words` 8-byte words global -> shared (coalesced, 16-byte loads when aligned), by a
-// CTA of kThreads threads.
-__device__ __forceinline__ void load_words(u64* dst, const u64* src, u64 words) {
-  const int tid = threadIdx.x;
-  if ((((uintptr_t)src) & 15) == 0) {
-    const u64 pairs = words >> 1;
-    const ulonglong2* s2 = reinterpret_cast<const ulonglong2*>(src);
-    ulonglong2* d2 = reinterpret_cast<ulonglong2*>(dst);
-    for (u64 i = tid; i < pairs; i += kThreads) d2[i] = __ldcs(s2 + i);
-    if ((words & 1) && tid == 0) dst[words - 1] = __ldcs(src + words - 1);
-  } else {
-    for (u64 i = tid; i < words; i += kThreads) dst[i] = __ldcs(src + i);
-  }
-}
-
-// Copy `words` words shared -> global, by a CTA of kThreads threads.
-__device__ __forceinline__ void store_words(u64* dst, const u64* src, u64 words) {
-  const int tid = threadIdx.x;
-  if ((((uintptr_t)dst) & 15) == 0) {
-    const u64 pairs = words >> 1;
-    const ulonglong2* s2 = reinterpret_cast<const ulonglong2*>(src);
-    ulonglong2* d2 = reinterpret_cast<ulonglong2*>(dst);
-    for (u64 i = tid; i < pairs; i += kThreads) d2[i] = s2[i];
-    if ((words & 1) && tid == 0) dst[words - 1] = src[words - 1];
-  } else {
-    for (u64 i = tid; i < words; i += kThreads) dst[i] = src[i];
-  }
-}
 
 // ------------------------------------------------------------------ launch helpers
 // Host-side launchers implemented in the kernel translation units.  Each returns the

@@ -140,7 +140,9 @@ rs_status radix_sort_release(void);
  * never the result.
  */
 typedef struct rs_plan {
-  uint32_t digit_bits_max;  /* widest digit of a distribution pass: 8..10 */
+  uint32_t digit_bits_max;  /* widest digit of a distribution pass: 8..10 (default 9, or 10 when
+                               that saves a level; each bin takes the fewest levels, then the
+                               narrowest digit for them) */
   uint32_t tile_records;    /* records per distribution tile: 256, 512, 1024, 2048 or 4096 */
   uint32_t chunk_records;   /* largest bin sorted on chip: 64.. the shared-memory maximum */
   uint32_t sm_limit;        /* use at most this many SMs for the persistent grids */

@@ -86,7 +86,18 @@ struct Shape {
 
 static Shape shape_for(u64 n, u32 rec_size, u32 key_size, const rs_plan& p) {
   Shape sh;
-  sh.wmax = p.digit_bits_max ? p.digit_bits_max : 9;
+  const u32 cap = chunk_capacity(rec_size / 8);
+  sh.chunk_max = p.chunk_records && p.chunk_records < cap ? p.chunk_records : cap;
+  // widest digit a level may use (it sizes the per-digit tables; each bin's digit is chosen by
+  // plan_digit: as few levels as possible, then the narrowest digit for them).  By default 9
+  // bits, or 10 when that saves a level for the whole input.
+  if (p.digit_bits_max) {
+    sh.wmax = p.digit_bits_max;
+  } else {
+    u32 need = 0;
+    while (need < 63 && (n >> need) > sh.chunk_max) need++;
+    sh.wmax = (need + 9) / 10 < (need + 8) / 9 ? 10 : 9;
+  }
   u32 T = 4096;  // 64 KB of 16-byte records per tile (measured best of 1024..4096)
   while (T > 256 && (u64)T * rec_size > 65536) T >>= 1;
   if (p.tile_records) T = p.tile_records;
@@ -94,9 +105,6 @@ static Shape shape_for(u64 n, u32 rec_size, u32 key_size, const rs_plan& p) {
   const u32 KW = key_size > 8 ? 2 : 1;
   while (T > 256 && level_smem_for(T, rec_size / 8, KW, sh.wmax) > kMaxSmemPerCta) T >>= 1;
   sh.T = T;
-  const u32 cap = chunk_capacity(rec_size / 8);
-  sh.chunk_max = p.chunk_records && p.chunk_records < cap ? p.chunk_records : cap;
-  (void)n;
   return sh;
 }
 

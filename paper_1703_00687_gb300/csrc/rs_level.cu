@@ -500,7 +500,7 @@ __global__ void __launch_bounds__(kSThreads, 2) k_scatter(Job j, int level) {
   constexpr u32 T = kSThreads * IT;
   constexpr u32 PW = T / kSWarps;  // records per warp strip
   constexpr u32 kDigitsPerThread = (1u << kWMax) / kSThreads;
-  const u32 WS = 1u << j.wmax;     // row stride of the per-warp counters
+  const u32 WSMAX = 1u << j.wmax;  // room for the per-warp counters: kSWarps rows of 2^wmax
   const ScatterLayout lay = scatter_layout(T, RW, j.wmax);
   extern __shared__ __align__(16) unsigned char smem[];
   u64* stage = (u64*)(smem + lay.stage);
@@ -513,8 +513,7 @@ __global__ void __launch_bounds__(kSThreads, 2) k_scatter(Job j, int level) {
   const u32 ltmask = lanemask_lt();
   // per-warp digit counters: counts while ranking, then each warp's offset inside the digit's
   // run; they are zeroed again while the tile is written out
-  for (u32 i = tid; i < kSWarps * WS; i += kSThreads) whist[i] = 0;
-  u16* wh = whist + warp * WS;
+  for (u32 i = tid; i < kSWarps * WSMAX; i += kSThreads) whist[i] = 0;
   const u64 per = lane_tiles(ntiles, j.lanes);
   bool inject = j.inject != 0 && blockIdx.x == 0 && tid == 0;  // testing: fail one run check
   __syncthreads();
@@ -529,6 +528,10 @@ __global__ void __launch_bounds__(kSThreads, 2) k_scatter(Job j, int level) {
       while (b + 1 < nb && bins[b + 1].tile_start <= t) b++;
       const Bin* bp = &bins[b];
       const u32 lo = bp->lo, W = bp->W, nd = 1u << W;
+    // per-warp counters with a row stride of this bin's digit count (every tile zeroes the
+    // rows it used, so the rows of a narrower or wider digit start at zero too)
+    const u32 WS = nd < 2 ? 2 : nd;
+    u16* wh = whist + warp * WS;
       const u64 begin = bp->begin, size = bp->size;
       const u64 tib = t - bp->tile_start;
       const u32 parity = bp->parity;

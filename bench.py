@@ -90,15 +90,24 @@ KERNEL_SOURCES = {"scatter": ["rs_level.cu", "rs_internal.cuh"], "hist": ["rs_le
                   "chunk": ["rs_chunk.cu", "rs_internal.cuh"]}
 
 
+def _code_only(text: str) -> str:
+    """C++ source without comments and blank space: what a kernel is compiled from."""
+    import re
+    text = re.sub(r"/\*.*?\*/", " ", text, flags=re.S)
+    text = re.sub(r"//[^\n]*", " ", text)
+    return " ".join(text.split())
+
+
 def kernel_source_sha(kernel=None):
-    """Hash of the sources a kernel is built from (all kernel sources when none is named)."""
+    """Hash of the code a kernel is built from (comments ignored; all kernel sources when none
+    is named)."""
     csrc = os.path.join(ROOT, "paper_1703_00687_gb300", "csrc")
     files = [os.path.join(csrc, f) for f in KERNEL_SOURCES[kernel]] if kernel in KERNEL_SOURCES else \
         sorted(glob.glob(os.path.join(csrc, "*")))
     h = hashlib.sha256()
     for p in files:
-        with open(p, "rb") as f:
-            h.update(f.read())
+        with open(p) as f:
+            h.update(_code_only(f.read()).encode())
     return h.hexdigest()[:16]
 
 

@@ -9,7 +9,10 @@
 //               differing key bit (digits shared by every key are skipped, the paper's
 //               remark in section 1 that bins of equal keys do not shrink), flags a recount
 //               if not, marks a bin of equal keys finished, and turns counts into bases.
-//   k_scatter   tile-wise stable scatter with a decoupled look-back across the tiles of a bin.
+//               It counts per lane (a contiguous range of the level's tiles), and the last
+//               CTA of a bin also turns every lane's counts into that lane's run starts.
+//   k_scatter   tile-wise stable scatter, lane by lane: a tile's destinations follow from its
+//               lane's run starts and the lane's earlier tiles (no CTA waits for another).
 //   k_classify  sub-bin classification, chunk packing, the next level's bin list.
 #include "rs_internal.cuh"
 

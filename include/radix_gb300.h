@@ -226,7 +226,7 @@ int64_t radix_sort_profile_read(rs_kernel_time *out, int64_t max);
  * Limits:
  *   The workspace needed for (n, rec_size, key_size) must fit the 64 MiB array, else the
  *   call returns RS_ERR_TOO_LARGE and launches nothing.  With the default plan that is about
- *   3.2 x 10^7 records of 16 bytes (8-byte keys), 3.7 x 10^7 of 8 bytes, 2.3 x 10^7 of
+ *   3.5 x 10^7 records of 16 bytes (8-byte keys), 3.7 x 10^7 of 8 bytes, 2.5 x 10^7 of
  *   24 bytes (16-byte keys).
  * Sharing:
  *   Every call uses the same array, on every stream.  Calls whose work overlaps on the GPU

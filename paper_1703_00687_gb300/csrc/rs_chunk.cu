@@ -31,7 +31,7 @@ constexpr int kEsMax = 48;       // largest bucket finished by enumeration sort
 constexpr int kWinBits = 12;     // digit of the on-chip distribution pass
 constexpr int kIdxBits = 13;     // input positions of a chunk (chunk_max <= 2^13)
 constexpr int kChunkItems = kChunkStages == 2 ? 8 : 10;  // positions per thread (chunk_max <= kCThreads * this)
-constexpr int kCntWords = 1 << (kIdxBits - 1);  // two 16-bit counters per word
+constexpr int kCntWords = 1 << (kWinBits - 1);  // counters of a distribution, two 16-bit per word
 // shared memory of the chunk CTA, and the part that is not per record
 constexpr size_t kChunkSmem = kChunkStages == 2 ? 220 * 1024 : 108 * 1024;
 constexpr size_t kChunkFixed = kCntWords * 4 + 4 * 1024;
@@ -60,7 +60,7 @@ struct ChunkCtx {
   const u64* stage;
   u16* perm;     // the current order (record indices)
   u16* out;      // scratch order
-  u32* cnt;      // 2^kIdxBits 16-bit counters, two per word
+  u32* cnt;      // 2^kWinBits 16-bit counters, two per word
   u32* stack;    // pairs (begin, size) of buckets still to sort
   u32 stack_cap;
 
@@ -74,7 +74,7 @@ struct ChunkCtx {
   __device__ __forceinline__ u32 count_of(u32 d) const { return (cnt[d >> 1] >> ((d & 1) * 16)) & 0xffffu; }
 };
 
-// Exclusive scan, in place, of nd (even, <= 2^kIdxBits) 16-bit counters packed two per word.
+// Exclusive scan, in place, of nd (even, <= 2^kWinBits) 16-bit counters packed two per word.
 template <int KW, int RWT>
 __device__ void scan_counts(const ChunkCtx<KW, RWT>& c, u32 nd) {
   __shared__ u32 scr[kCWarps + 1];
@@ -280,6 +280,7 @@ __device__ void restore_input_order(const ChunkCtx<KW, RWT>& c, u32 a, u32 s) {
   __shared__ u32 scr[kCWarps];
   constexpr u32 kWords = (1u << kIdxBits) / 32;  // bitmap words over every possible index
   static_assert(kWords <= (u32)kCThreads, "one bitmap word per thread");
+  static_assert(2 * kWords <= (u32)kCntWords, "bitmap and prefix fit the counters");
   u32* bm = c.cnt;             // [kWords] the bitmap
   u32* below = c.cnt + kWords;  // [kWords] marked indices in the words before
   const u32 tid = threadIdx.x;

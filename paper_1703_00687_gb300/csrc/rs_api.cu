@@ -298,7 +298,7 @@ static int timed(u32 kernel, u32 level, cudaStream_t s, F&& launch) {
 static rs_status run_levels(const Setup& st, cudaStream_t s) {
   const Job& j = st.j;
   const u32 gs = (u32)st.sms * (u32)scatter_ctas_per_sm(j);
-  const u32 gc = (u32)st.sms * 2;
+  const u32 gc = (u32)st.sms * (u32)classify_ctas_per_sm();
   const int levels = (int)j.K;  // each level consumes >= 8 key bits
   for (int lv = 0; lv < levels; lv++) {
     if (timed(RS_K_HIST, lv, s, [&] { return launch_hist(j, lv, 0, s); }) < 0) return RS_ERR_CUDA;
@@ -390,7 +390,7 @@ static void noalloc_carve(Setup* st, char* base) {
 static rs_status noalloc_levels(const Setup& st, cudaStream_t s) {
   const Job& j = st.j;
   const u32 gs = (u32)st.sms * (u32)scatter_ctas_per_sm(j);
-  const u32 gc = (u32)st.sms * 2;
+  const u32 gc = (u32)st.sms * (u32)classify_ctas_per_sm();
   int k;
   for (int lv = 0; lv < (int)j.K; lv++) {
     if ((k = launch_hist(j, lv, 0, s)) < 0) return RS_ERR_CUDA;

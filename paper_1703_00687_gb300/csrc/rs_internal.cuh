@@ -302,5 +302,6 @@ size_t chunk_smem_bytes(const Job& j);
 int scatter_ctas_per_sm(const Job& j);
 int chunk_ctas_per_sm(const Job& j);
 int hist_ctas_per_sm(const Job& j);
+int classify_ctas_per_sm();
 
 }  // namespace rsg

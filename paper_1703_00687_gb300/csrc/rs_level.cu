@@ -18,9 +18,11 @@
 
 namespace rsg {
 
-// Exclusive scan of one u64 per thread (kThreads threads); returns the exclusive prefix and
-// the total in *total.
+// Exclusive scan of one u64 per thread (NT threads); returns the exclusive prefix and the
+// total in *total.  scratch holds NT / 32 + 1 words.
+template <int NT = kThreads>
 __device__ inline u64 block_scan_value64(u64 x, u64* scratch, u64* total) {
+  constexpr int kW = NT / 32;
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
   u64 s = x;
 #pragma unroll
@@ -31,37 +33,49 @@ __device__ inline u64 block_scan_value64(u64 x, u64* scratch, u64* total) {
   if (lane == 31) scratch[warp] = s;
   __syncthreads();
   if (warp == 0) {
-    u64 w = lane < kWarps ? scratch[lane] : 0, t = w;
+    u64 w = lane < kW ? scratch[lane] : 0, t = w;
 #pragma unroll
     for (int o = 1; o < 32; o <<= 1) {
       u64 y = __shfl_up_sync(kFull, t, o);
       if (lane >= o) t += y;
     }
-    if (lane < kWarps) scratch[lane] = t - w;
-    if (lane == kWarps - 1) scratch[kWarps] = t;
+    if (lane < kW) scratch[lane] = t - w;
+    if (lane == kW - 1) scratch[kW] = t;
   }
   __syncthreads();
   u64 r = scratch[warp] + s - x;
-  *total = scratch[kWarps];
+  *total = scratch[kW];
   __syncthreads();
   return r;
 }
 
 // Tile numbering of bin list L: tile_start = exclusive prefix of ceil(size / T) in list order.
-// One CTA of kThreads threads.
+// One CTA of NT threads; each thread takes kItems consecutive bins per round, so that their
+// loads are in flight together.
+template <int NT = kThreads>
 __device__ void finalize_list(const Job& j, int L) {
-  __shared__ u64 scr[kWarps + 1];
+  constexpr int kItems = 4;
+  __shared__ u64 scr[NT / 32 + 1];
   Ctl* ctl = j.ctl;
   u64 nb = *(volatile u64*)&ctl->nbins[L];
   if (nb > j.cap_bins) nb = j.cap_bins;
   Bin* bins = j.bins[L];
   u64 carry = 0;
-  for (u64 base = 0; base < nb; base += kThreads) {
-    const u64 i = base + threadIdx.x;
-    const u64 t = i < nb ? ceil_div(bins[i].size, j.T) : 0;
+  for (u64 base = 0; base < nb; base += (u64)NT * kItems) {
+    const u64 i0 = base + (u64)threadIdx.x * kItems;
+    u64 t[kItems], sum = 0;
+#pragma unroll
+    for (int q = 0; q < kItems; q++) {
+      t[q] = i0 + q < nb ? ceil_div(bins[i0 + q].size, j.T) : 0;
+      sum += t[q];
+    }
     u64 tot;
-    const u64 ex = block_scan_value64(t, scr, &tot);
-    if (i < nb) bins[i].tile_start = carry + ex;
+    u64 ex = carry + block_scan_value64<NT>(sum, scr, &tot);
+#pragma unroll
+    for (int q = 0; q < kItems; q++) {
+      if (i0 + q < nb) bins[i0 + q].tile_start = ex;
+      ex += t[q];
+    }
     carry += tot;
   }
   if (threadIdx.x == 0) {
@@ -706,6 +720,7 @@ template <int KW>
 __device__ u32 sample_top_bit(const Job& j, const u64* rec, u64 c) {
   u64 a[2] = {~0ull, ~0ull}, o[2] = {0, 0};
   const int ns = 32;
+#pragma unroll(8 / KW)
   for (int i = 0; i < ns; i++) {
     const u64 r = (c * (u64)i) / ns;
     const Key<KW> k = load_key<KW>(rec + r * j.RW, j);
@@ -734,24 +749,74 @@ __device__ void push_pieces(const Job& j, u64 begin, u64 c) {
   }
 }
 
+// Bit sets of sub-bins, 32 to a word.
+// First member >= u of a set of nb bits, nb if none.
+__device__ __forceinline__ u32 next_member(const u32* m, u32 u, u32 nb) {
+  if (u >= nb) return nb;
+  const u32 nw = (nb + 31) >> 5;
+  u32 w = u >> 5, x = m[w] & (~0u << (u & 31));
+  while (x == 0) {
+    if (++w >= nw) return nb;
+    x = m[w];
+  }
+  return (w << 5) + __ffs(x) - 1;
+}
+// Last member <= u (u itself if none is found before word 0 runs out).
+__device__ __forceinline__ u32 prev_member(const u32* m, u32 u) {
+  u32 w = u >> 5, x = m[w] & ((u & 31) == 31 ? ~0u : (2u << (u & 31)) - 1);
+  while (x == 0) {
+    if (w == 0) return u;
+    x = m[--w];
+  }
+  return (w << 5) + 31 - __clz(x);
+}
+// Whether any of [a, b] is a member.
+__device__ __forceinline__ bool any_member(const u32* m, u32 a, u32 b) {
+  const u32 wa = a >> 5, wb = b >> 5;
+  for (u32 w = wa; w <= wb; w++) {
+    u32 x = m[w];
+    if (w == wa) x &= ~0u << (a & 31);
+    if (w == wb) x &= (b & 31) == 31 ? ~0u : (2u << (b & 31)) - 1;
+    if (x) return true;
+  }
+  return false;
+}
+
+constexpr int kClsThreads = 256;
+constexpr int kClsCtas = 4;  // per SM: a bin is a chain of dependent loads and barriers
+constexpr u16 kKeepChunk = 0x8000;
+
+// Per bin of the level, for every sub-bin v of its digit: empty, one record (finished where
+// it is), 2..chunk_max records (sorted on chip), or more (a bin of the next level, whose
+// digit is guessed from a sample).  Consecutive sub-bins of at most chunk_max records are
+// packed greedily into chunks of at most chunk_max records: a chunk opens at a non-empty
+// small sub-bin and takes the following ones while they fit; a large sub-bin closes it.
+// The packing runs in parallel: S = inclusive prefix of the sizes (a large sub-bin counts
+// chunk_max + 1, so no chunk reaches past it), the chunk opened at v ends at the last e with
+// S[e] <= S[v - 1] + chunk_max, and the next chunk opens at the first small sub-bin after e;
+// one thread then follows that chain from the first small sub-bin.  A chunk made only of
+// single records that are already in `in` is finished and not kept.
 template <int KW>
-__global__ void __launch_bounds__(kThreads) k_classify(Job j, int level) {
+__global__ void __launch_bounds__(kClsThreads, kClsCtas) k_classify(Job j, int level) {
   const int L = level & 1, N = L ^ 1;
   Ctl* ctl = j.ctl;
   const u64 nb = ctl->nbins[L];
   if (nb == 0) return;
   const Bin* bins = j.bins[L];
-  __shared__ u8 cls[1 << kWMax];
-  __shared__ u32 cnt[1 << kWMax];
-  __shared__ u64 boff[1 << kWMax];
-  // the bin's chunks, packed by thread 0, then reserved with one atomic and written by all
-  __shared__ u32 pk_first[1 << kWMax];  // first sub-bin | (1 << 31) if any needs sorting
-  __shared__ u16 pk_last[1 << kWMax];   // last sub-bin
-  __shared__ u32 pk_size[1 << kWMax];
+  constexpr u32 kMaxD = 1u << kWMax;
+  __shared__ u32 S[kMaxD];              // inclusive prefix of sub-bin sizes
+  __shared__ u64 boff[kMaxD];           // first record of sub-bin v within the bin
+  __shared__ u16 vlast[kMaxD];          // chunk opened at v: its last non-empty sub-bin
+  __shared__ u16 vnext[kMaxD];          // chunk opened at v: where the next opens | kKeepChunk
+  __shared__ u16 pk[kMaxD];             // the bin's kept chunks: first sub-bin
+  __shared__ u32 m12[kMaxD / 32];       // sub-bins of 1..chunk_max records
+  __shared__ u32 m2[kMaxD / 32];        // sub-bins of 2..chunk_max records
+  __shared__ u32 scr[kClsThreads / 32];
   __shared__ u32 s_npk;
   __shared__ u64 s_base;
   __shared__ int s_last;
-  const int tid = threadIdx.x;
+  const int tid = threadIdx.x, lane = tid & 31;
+  const u32 cm = j.chunk_max;
   for (u64 b = blockIdx.x; b < nb; b += gridDim.x) {
     const Bin bin = bins[b];
     if (bin.flags & kBinEqual) {  // finished without moving; copy back if it lives in tmp
@@ -761,88 +826,87 @@ __global__ void __launch_bounds__(kThreads) k_classify(Job j, int level) {
     const u32 nd = 1u << bin.W;
     const u32 p1 = bin.parity ^ 1;
     const u64* bbase = j.base[L] + bin.base_off;
-    for (u32 v = tid; v < nd; v += kThreads) {
-      u64 bv = bbase[v];
-      u64 next = v + 1 < nd ? bbase[v + 1] : bin.size;
-      if (next < bv || next > bin.size) {  // inconsistent bases (only after a reported error)
-        atomicOr(&ctl->err, kErrInternal);
-        next = bv = min(bv, bin.size);
-      }
-      const u64 c = next - bv;
-      boff[v] = bv;
-      cnt[v] = (u32)min(c, (u64)j.chunk_max + 1);
-      u8 k;
-      if (c == 0) {
-        k = 0;
-      } else if (c == 1) {
-        k = 1;
-      } else if (c <= j.chunk_max) {
-        k = 2;
-      } else {
-        k = 3;
-        const u64 rb = bin.begin + bv;
-        // every key bit >= bin.lo is shared by the sub-bin; guess where its next digit
-        // starts from a sample
-        u32 p = sample_top_bit<KW>(j, j.buf[p1] + rb * j.RW, c);
-        if (p == 0 || p > bin.lo) p = bin.lo;
-        if (p == 0) p = 1;
-        u32 nlo, nW;
-        plan_digit(c, p, j.chunk_max, j.wmax, &nlo, &nW);
-        const u32 nnd = 1u << nW;
-        const u64 idx = atomicAdd(&ctl->nbins[N], 1ull);
-        const u64 bo = atomicAdd(&ctl->base_used[N], (u64)nnd);
-        if (idx >= j.cap_bins || bo + nnd > j.cap_base) {
-          atomicOr(&ctl->err, kErrOverflow);
-        } else {
-          Bin nbn = {};
-          nbn.begin = rb;
-          nbn.size = c;
-          nbn.base_off = bo;
-          nbn.kand[0] = nbn.kand[1] = ~0ull;
-          nbn.lo = nlo;
-          nbn.W = nW;
-          nbn.parity = p1;
-          j.bins[N][idx] = nbn;
-          for (u32 q = 0; q < nnd; q++) j.base[N][bo + q] = 0;
+    for (u32 v0 = tid & ~31u; v0 < nd; v0 += kClsThreads) {
+      const u32 v = v0 + lane;
+      u32 k = 0;
+      if (v < nd) {
+        u64 bv = bbase[v];
+        u64 next = v + 1 < nd ? bbase[v + 1] : bin.size;
+        if (next < bv || next > bin.size) {  // inconsistent bases (only after a reported error)
+          atomicOr(&ctl->err, kErrInternal);
+          next = bv = min(bv, bin.size);
+        }
+        const u64 c = next - bv;
+        boff[v] = bv;
+        k = c == 0 ? 0 : c == 1 ? 1 : c <= cm ? 2 : 3;
+        S[v] = k == 3 ? cm + 1 : (u32)c;
+        if (k == 3) {
+          const u64 rb = bin.begin + bv;
+          // every key bit >= bin.lo is shared by the sub-bin; guess where its next digit
+          // starts from a sample
+          u32 p = sample_top_bit<KW>(j, j.buf[p1] + rb * j.RW, c);
+          if (p == 0 || p > bin.lo) p = bin.lo;
+          if (p == 0) p = 1;
+          u32 nlo, nW;
+          plan_digit(c, p, cm, j.wmax, &nlo, &nW);
+          const u32 nnd = 1u << nW;
+          const u64 idx = atomicAdd(&ctl->nbins[N], 1ull);
+          const u64 bo = atomicAdd(&ctl->base_used[N], (u64)nnd);
+          if (idx >= j.cap_bins || bo + nnd > j.cap_base) {
+            atomicOr(&ctl->err, kErrOverflow);
+          } else {
+            Bin nbn = {};
+            nbn.begin = rb;
+            nbn.size = c;
+            nbn.base_off = bo;
+            nbn.kand[0] = nbn.kand[1] = ~0ull;
+            nbn.lo = nlo;
+            nbn.W = nW;
+            nbn.parity = p1;
+            j.bins[N][idx] = nbn;
+            for (u32 q = 0; q < nnd; q++) j.base[N][bo + q] = 0;
+          }
         }
       }
-      cls[v] = k;
+      const u32 small = __ballot_sync(kFull, k == 1 || k == 2), multi = __ballot_sync(kFull, k == 2);
+      if (lane == 0) {
+        m12[v0 >> 5] = small;
+        m2[v0 >> 5] = multi;
+      }
+    }
+    __syncthreads();
+    {  // S: sizes -> inclusive prefix (at most 2^kWMax * (chunk_max + 1), well inside u32)
+      const u32 ipt = (nd + kClsThreads - 1) / kClsThreads, v0 = tid * ipt;
+      u32 own = 0;
+      for (u32 q = 0; q < ipt; q++)
+        if (v0 + q < nd) own += S[v0 + q];
+      u32 run = block_exclusive_sum<kClsThreads>(own, scr);  // ends with a barrier
+      for (u32 q = 0; q < ipt; q++)
+        if (v0 + q < nd) S[v0 + q] = run += S[v0 + q];
+    }
+    __syncthreads();
+    for (u32 v = tid; v < nd; v += kClsThreads) {
+      if (!(m12[v >> 5] >> (v & 31) & 1u)) continue;
+      const u32 lim = (v ? S[v - 1] : 0) + cm;
+      u32 lo = v, hi = nd;  // S[lo] <= lim (a small sub-bin fits alone), S[hi] > lim or hi = nd
+      while (hi - lo > 1) {
+        const u32 mid = (lo + hi) >> 1;
+        if (S[mid] <= lim) lo = mid; else hi = mid;
+      }
+      const u32 vl = prev_member(m12, lo);
+      const bool keep = p1 || any_member(m2, v, vl);
+      vlast[v] = (u16)vl;
+      vnext[v] = (u16)(next_member(m12, lo + 1, nd) | (keep ? kKeepChunk : 0u));
     }
     __syncthreads();
     if (tid == 0) {
-      // greedy packing of consecutive small sub-bins into on-chip chunks (a chunk made only
-      // of single records, already in `in`, is finished and not kept)
-      u32 npk = 0, csz = 0, vfirst = 0, vlast = 0;
-      bool open = false, uns = false;
-      auto emit = [&]() {
-        if (open && (uns || p1)) {
-          pk_first[npk] = vfirst | (uns ? 0x80000000u : 0u);
-          pk_last[npk] = (u16)vlast;
-          pk_size[npk] = csz;
-          npk++;
-        }
-        open = false;
-      };
-      for (u32 v = 0; v < nd; v++) {
-        const u8 k = cls[v];
-        if (k == 0) continue;
-        if (k <= 2) {
-          const u32 sz = cnt[v];
-          if (open && csz + sz > j.chunk_max) emit();
-          if (!open) {
-            csz = 0;
-            vfirst = v;
-            uns = false;
-            open = true;
-          }
-          csz += sz;
-          vlast = v;
-          if (k == 2) uns = true;
-        } else {
-          emit();
-        }
+      u32 npk = 0;
+      for (u32 v = next_member(m12, 0, nd); v < nd;) {
+        const u32 x = vnext[v];
+        if (x & kKeepChunk) pk[npk++] = (u16)v;
+        const u32 w = x & ~(u32)kKeepChunk;
+        v = w > v ? w : nd;
       }
-      emit();
       s_npk = npk;
       s_base = npk ? atomicAdd(&ctl->nchunks, (u64)npk) : 0;
     }
@@ -853,13 +917,12 @@ __global__ void __launch_bounds__(kThreads) k_classify(Job j, int level) {
       if (base + npk > j.cap_chunks) {
         if (tid == 0 && npk) atomicOr(&ctl->err, kErrOverflow);
       } else {
-        for (u32 q = tid; q < npk; q += kThreads) {
-          const u32 vf = pk_first[q] & 0x7fffffffu, vl = pk_last[q];
-          const bool uns = (pk_first[q] >> 31) != 0;
+        for (u32 q = tid; q < npk; q += kClsThreads) {
+          const u32 vf = pk[q], vl = vlast[vf];
           Chunk ch = {};
           ch.begin = bin.begin + boff[vf];
-          ch.size = pk_size[q];
-          ch.flags = (p1 ? kChSrcTmp : 0u) | (uns ? 0u : kChCopyOnly);
+          ch.size = S[vl] - (vf ? S[vf - 1] : 0);
+          ch.flags = (p1 ? kChSrcTmp : 0u) | (any_member(m2, vf, vl) ? 0u : kChCopyOnly);
           // one sub-bin shares every bit >= lo; several differ in the digit itself
           ch.p = bin.lo;
           ch.pw = (u16)bin.W;
@@ -882,7 +945,7 @@ __global__ void __launch_bounds__(kThreads) k_classify(Job j, int level) {
   __syncthreads();
   if (s_last) {
     __threadfence();
-    finalize_list(j, N);
+    finalize_list<kClsThreads>(j, N);
     if (tid == 0) {
       ctl->cls_done = 0;
       ctl->nredo = 0;
@@ -1005,9 +1068,11 @@ int launch_scatter(const Job& j, int level, u32 grid, cudaStream_t s) {
   return e == cudaSuccess ? 1 : -1;
 }
 
+int classify_ctas_per_sm() { return kClsCtas; }
+
 int launch_classify(const Job& j, int level, u32 grid, cudaStream_t s) {
-  if (j.KW == 1) k_classify<1><<<grid, kThreads, 0, s>>>(j, level);
-  else k_classify<2><<<grid, kThreads, 0, s>>>(j, level);
+  if (j.KW == 1) k_classify<1><<<grid, kClsThreads, 0, s>>>(j, level);
+  else k_classify<2><<<grid, kClsThreads, 0, s>>>(j, level);
   return cudaGetLastError() == cudaSuccess ? 1 : -1;
 }
 

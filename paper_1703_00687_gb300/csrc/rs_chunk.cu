@@ -490,10 +490,27 @@ __global__ void __launch_bounds__(kCThreads, kChunkCtas) k_chunk(Job j) {
           const ulonglong2 v = *reinterpret_cast<const ulonglong2*>(stage + 2 * (u64)r);
           __stcs(reinterpret_cast<ulonglong2*>(dst + 2 * (u64)s), v);
         }
-      } else if (RWT != 0) {
+      } else if (RWT != 0 && (RW & 1)) {
         for (u32 q = tid; q < sz * RW; q += kCThreads) {
           const u32 s = q / RW, w = q - s * RW;
           __stcs(dst + q, stage[(u64)c.perm[s] * RW + w]);
+        }
+      } else if (RW <= 32) {
+        // whole warps write consecutive records: lane k * P + piece moves one piece (16 bytes
+        // if RW is even, else 8) of record s0 + k
+        const int lane = tid & 31, warp = tid >> 5;
+        const bool pairs = (RW & 1) == 0;
+        const u32 P = pairs ? RW >> 1 : RW, rpw = 32 / P;
+        const u32 k = lane / P, piece = lane - k * P;
+        for (u32 s0 = warp * rpw; s0 < sz; s0 += kCWarps * rpw) {
+          const u32 s = s0 + k;
+          if (k >= rpw || s >= sz) continue;
+          const u64* sp = stage + (u64)c.perm[s] * RW;
+          u64* d = dst + (u64)s * RW;
+          if (pairs)
+            __stcs(reinterpret_cast<ulonglong2*>(d) + piece, reinterpret_cast<const ulonglong2*>(sp)[piece]);
+          else
+            __stcs(d + piece, sp[piece]);
         }
       } else {
         for (u32 s = tid; s < sz; s += kCThreads) {

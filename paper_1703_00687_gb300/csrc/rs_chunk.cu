@@ -495,9 +495,9 @@ __global__ void __launch_bounds__(kCThreads, kChunkCtas) k_chunk(Job j) {
           const u32 s = q / RW, w = q - s * RW;
           __stcs(dst + q, stage[(u64)c.perm[s] * RW + w]);
         }
-      } else if (RW <= 32) {
+      } else {
         // whole warps write consecutive records: lane k * P + piece moves one piece (16 bytes
-        // if RW is even, else 8) of record s0 + k
+        // if RW is even, else 8) of record s0 + k (P <= 32: records are at most 256 bytes)
         const int lane = tid & 31, warp = tid >> 5;
         const bool pairs = (RW & 1) == 0;
         const u32 P = pairs ? RW >> 1 : RW, rpw = 32 / P;
@@ -511,11 +511,6 @@ __global__ void __launch_bounds__(kCThreads, kChunkCtas) k_chunk(Job j) {
             __stcs(reinterpret_cast<ulonglong2*>(d) + piece, reinterpret_cast<const ulonglong2*>(sp)[piece]);
           else
             __stcs(d + piece, sp[piece]);
-        }
-      } else {
-        for (u32 s = tid; s < sz; s += kCThreads) {
-          const u64* sp = stage + (u64)c.perm[s] * RW;
-          for (u32 w = 0; w < RW; w++) __stcs(dst + (u64)s * RW + w, sp[w]);
         }
       }
     } else {

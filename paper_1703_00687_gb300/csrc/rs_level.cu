@@ -698,9 +698,10 @@ __global__ void __launch_bounds__(kSThreads, 2) k_scatter(Job j, int level) {
           if (g == kSkip) continue;
           __stcs(reinterpret_cast<ulonglong2*>(dstb + 2 * (g + s)), v);
         }
-      } else if (RW <= 32) {
+      } else {
         // whole warps write consecutive slots: lane k * P + piece moves one piece (16 bytes if
         // RW is even, else 8) of slot s0 + k, so a store instruction covers whole records of a run
+        // (P <= 32: records are at most 256 bytes)
         const bool pairs = (RW & 1) == 0;
         const u32 P = pairs ? RW >> 1 : RW, rpw = 32 / P;
         const u32 k = lane / P, piece = lane - k * P;
@@ -716,15 +717,6 @@ __global__ void __launch_bounds__(kSThreads, 2) k_scatter(Job j, int level) {
             __stcs(reinterpret_cast<ulonglong2*>(d) + piece, reinterpret_cast<const ulonglong2*>(sp)[piece]);
           else
             __stcs(d + piece, sp[piece]);
-        }
-      } else {
-        for (u32 s = tid; s < cnt; s += kSThreads) {
-          const u32 sw = slotw[s];
-          const u64 g = gbase[sw >> 16];
-          if (g == kSkip) continue;
-          const u64* sp = stage + (u64)(sw & 0xffffu) * RW;
-          u64* d = dstb + (g + s) * RW;
-          for (u32 w = 0; w < RW; w++) __stcs(d + w, sp[w]);
         }
       }
       __syncthreads();

@@ -58,7 +58,9 @@ def test_histogram_parity(R, K, lo, w):
 
 
 # ---------------------------------------------------------------------- sort
-LAYOUTS = [(8, 8), (8, 1), (8, 5), (16, 8), (16, 16), (24, 16), (32, 8), (40, 13), (64, 16), (256, 9)]
+# record sizes of every write path: 8 and 16 bytes (one store per record), 24/40 (whole warps,
+# 8-byte pieces), 32/48/64/256 (whole warps, 16-byte pieces; 256 bytes is the largest record)
+LAYOUTS = [(8, 8), (8, 1), (8, 5), (16, 8), (16, 16), (24, 16), (32, 8), (40, 13), (48, 16), (64, 16), (256, 9)]
 
 
 @pytest.mark.parametrize("R,K", LAYOUTS)

@@ -31,7 +31,7 @@ class RsKernelTime(ctypes.Structure):
     _fields_ = [("kernel", ctypes.c_uint32), ("level", ctypes.c_uint32), ("ms", ctypes.c_float)]
 
 
-KERNEL_NAMES = {0: "init", 1: "hist", 2: "hist_redo", 3: "scatter", 4: "classify", 5: "chunk", 6: "copy"}
+KERNEL_NAMES = {0: "init", 1: "hist", 2: "hist_redo", 3: "scatter", 4: "classify", 5: "chunk", 6: "copy", 7: "tiny"}
 
 SIGNATURES = {
     "radix_sort": (_i32, [_vp, _vp, _u64, _u32, _u32, _vp]),

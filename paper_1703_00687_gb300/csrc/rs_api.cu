@@ -308,6 +308,7 @@ static rs_status run_levels(const Setup& st, cudaStream_t s) {
   }
   const u32 gch = (u32)st.sms * (u32)chunk_ctas_per_sm(j);
   if (timed(RS_K_CHUNK, levels, s, [&] { return launch_chunks(j, gch, s); }) < 0) return RS_ERR_CUDA;
+  if (timed(RS_K_TINY, levels, s, [&] { return launch_tiny(j, (u32)st.sms, s); }) < 0) return RS_ERR_CUDA;
   if (timed(RS_K_COPY, levels, s, [&] { return launch_copy(j, (u32)st.sms * 2, s); }) < 0) return RS_ERR_CUDA;
   return RS_OK;
 }
@@ -403,6 +404,8 @@ static rs_status noalloc_levels(const Setup& st, cudaStream_t s) {
     count(k);
   }
   if ((k = launch_chunks(j, (u32)st.sms * (u32)chunk_ctas_per_sm(j), s)) < 0) return RS_ERR_CUDA;
+  count(k);
+  if ((k = launch_tiny(j, (u32)st.sms, s)) < 0) return RS_ERR_CUDA;
   count(k);
   if ((k = launch_copy(j, (u32)st.sms * 2, s)) < 0) return RS_ERR_CUDA;
   count(k);

@@ -16,6 +16,8 @@
 //     back in input order (ranks of its input positions, from a bitmap of them);
 //   * a chunk of at most kEsMax records is one enumeration sort, without a distribution.
 // The result is therefore the stable order, and the whole sorter is stable.
+#include <algorithm>
+
 #include "rs_internal.cuh"
 
 namespace rsg {
@@ -353,6 +355,10 @@ __global__ void __launch_bounds__(kCThreads, kChunkCtas) k_chunk(Job j) {
   Ctl* ctl = j.ctl;
   const u64 nch = ctl->nchunks;
   if (nch == 0) return;
+  if (nch + ctl->ntiny > j.cap_chunks) {  // the two lists met (reported when they were filled)
+    if (blockIdx.x == 0 && threadIdx.x == 0) atomicOr(&ctl->err, kErrOverflow);
+    return;
+  }
   const u32 RW = RWT ? (u32)RWT : j.RW;
   const u32 m = j.chunk_max;
   const ChunkLayout lay = chunk_layout(m, RW);
@@ -599,6 +605,226 @@ int chunk_ctas_per_sm(const Job& j) {
 
 int launch_chunks(const Job& j, u32 grid, cudaStream_t s) {
   cudaError_t e = j.KW == 1 ? launch_chunks_kw<1>(j, grid, s) : launch_chunks_kw<2>(j, grid, s);
+  return e == cudaSuccess ? 1 : -1;
+}
+
+// ------------------------------------------------------------------------------ tiny
+// Chunks of at most kTinyMax = 64 records (tiny segments of a batched sort, short packed runs):
+// warps instead of CTAs (the paper's tiny-array sorter, section 2.2).  A warp reads the
+// descriptors of 32 consecutive tiny chunks at once (one per lane), then sorts them in rounds:
+// a chunk of more than 32 records takes the whole warp (tiny_sort64); otherwise a round takes
+// the next G chunks that all fit in w = 32 / G records (w a power of two), one group of w
+// lanes per chunk, and
+//   * stages each lane's record in the warp's slice of shared memory (so a chunk may be sorted
+//     in place),
+//   * sorts every group's pairs (key, input position) ascending with a bitonic network over
+//     its w lanes -- compare-exchange partners by shuffles; the position breaks ties, so the
+//     order is the stable one; lanes past a chunk's end hold the largest key and positions
+//     past every real one, so they sort last --
+//   * and writes lane r's output record r of its chunk from the slice.
+// Warps take batches of chunks by a static stride (tiny chunks are all alike).
+constexpr int kTinyThreads = 256;
+constexpr int kTinyWarps = kTinyThreads / 32;
+
+// One chunk of 33..64 records by one warp: lane l holds records l and l + 32 (the second pair
+// of the bitonic network's elements); the stages that pair element e with e + 32 compare
+// within a lane, the others exchange both elements by shuffles.
+template <int KW>
+__device__ __forceinline__ void tiny_sort64(const Job& j, u64 begin, u32 size, u32 flags, const u64* slice,
+                                            u32 lane) {
+  const u32 RW = j.RW;
+  u64* sl = const_cast<u64*>(slice);
+  const u64* src = j.buf[(flags & kChSrcTmp) ? 1 : 0] + begin * RW;
+  u64* dst = j.buf[0] + begin * RW;
+  if (flags & kChCopyOnly) {  // in order already; copy it to `in` if it lives in tmp
+    if (flags & kChSrcTmp)
+      for (u32 q = lane; q < size * RW; q += 32) __stcs(dst + q, src[q]);
+    return;
+  }
+  for (u32 q = lane; q < size * RW; q += 32) sl[q] = src[q];
+  __syncwarp();
+  Key<KW> ka, kb;
+  u32 ia = lane, ib = lane + 32;
+#pragma unroll
+  for (int q = 0; q < KW; q++) ka.w[q] = kb.w[q] = ~0ull;
+  if (ia < size) {
+    ka.w[0] = sl[ia * RW] & j.keymask[0];
+    if (KW == 2) ka.w[KW - 1] = sl[ia * RW + 1] & j.keymask[1];
+  }
+  if (ib < size) {
+    kb.w[0] = sl[ib * RW] & j.keymask[0];
+    if (KW == 2) kb.w[KW - 1] = sl[ib * RW + 1] & j.keymask[1];
+  }
+  auto less = [](const Key<KW>& x, u32 xi, const Key<KW>& y, u32 yi) {
+    return key_less<KW>(x, y) || (key_eq<KW>(x, y) && xi < yi);
+  };
+  // one compare-exchange of element e (key k, position i) with its partner across lanes
+  auto cross = [&](Key<KW>& k, u32& i, u32 e, u32 blk, u32 d) {
+    Key<KW> o;
+#pragma unroll
+    for (int q = 0; q < KW; q++) o.w[q] = __shfl_xor_sync(kFull, k.w[q], d);
+    const u32 oi = __shfl_xor_sync(kFull, i, d);
+    const bool o_less = less(o, oi, k, i);
+    const bool ascending = (e & blk) == 0, lower = (e & d) == 0;
+    if (ascending == lower ? o_less : !o_less) {
+      k = o;
+      i = oi;
+    }
+  };
+#pragma unroll
+  for (u32 blk = 2; blk <= 64; blk <<= 1) {
+#pragma unroll
+    for (u32 d = blk >> 1; d > 0; d >>= 1) {
+      if (d == 32) {  // elements lane and lane + 32: the lower one keeps the smaller (blk = 64)
+        if (less(kb, ib, ka, ia)) {
+          const Key<KW> tk = ka;
+          ka = kb;
+          kb = tk;
+          const u32 ti = ia;
+          ia = ib;
+          ib = ti;
+        }
+      } else {
+        cross(ka, ia, lane, blk, d);
+        cross(kb, ib, lane + 32, blk, d);
+      }
+    }
+  }
+  // output record e = input record i_e
+  const u32 outs[2] = {lane, lane + 32}, from[2] = {ia, ib};
+#pragma unroll
+  for (int h = 0; h < 2; h++) {
+    if (outs[h] >= size) continue;
+    const u64* sp = slice + (size_t)from[h] * RW;
+    u64* dp = dst + (u64)outs[h] * RW;
+    if ((RW & 1) == 0) {
+      for (u32 q = 0; q < RW; q += 2)
+        __stcs(reinterpret_cast<ulonglong2*>(dp + q), *reinterpret_cast<const ulonglong2*>(sp + q));
+    } else {
+      for (u32 q = 0; q < RW; q++) __stcs(dp + q, sp[q]);
+    }
+  }
+  __syncwarp();  // the slice is reused by the next chunk
+}
+
+template <int KW>
+__global__ void __launch_bounds__(kTinyThreads) k_tiny(Job j) {
+  Ctl* ctl = j.ctl;
+  const u64 nt = ctl->ntiny;
+  if (nt == 0) return;
+  if (ctl->nchunks + nt > j.cap_chunks) {  // the two lists met (reported when they were filled)
+    if (blockIdx.x == 0 && threadIdx.x == 0) atomicOr(&ctl->err, kErrOverflow);
+    return;
+  }
+  extern __shared__ __align__(16) unsigned char smem[];
+  const u32 RW = j.RW;
+  const u32 lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  u64* mine = reinterpret_cast<u64*>(smem) + ((size_t)warp * kTinyMax + lane) * RW;  // this lane's record
+  const u64* slice = reinterpret_cast<const u64*>(smem) + (size_t)warp * kTinyMax * RW;
+  const u64 warps = (u64)gridDim.x * kTinyWarps;
+  for (u64 t0 = ((u64)blockIdx.x * kTinyWarps + warp) * 32; t0 < nt; t0 += warps * 32) {
+    const u32 nb = (u32)min((u64)32, nt - t0);
+    // lane i: descriptor of chunk t0 + i (an unusable one is reported and left out)
+    u64 c_begin = 0;
+    u32 c_size = 0, c_flags = 0;
+    if (lane < nb) {
+      const Chunk ch = j.chunks[j.cap_chunks - 1 - (t0 + lane)];
+      if (ch.size > kTinyMax || ch.begin > j.n || ch.begin + ch.size > j.n) {
+        atomicOr(&ctl->err, kErrInternal);
+      } else {
+        c_begin = ch.begin;
+        c_size = ch.size;
+        c_flags = ch.flags;
+      }
+    }
+    // fits[q]: lanes whose chunk holds at most 2^q records
+    u32 fits[6];
+#pragma unroll
+    for (int q = 1; q <= 5; q++) fits[q] = __ballot_sync(kFull, c_size <= (1u << q)) | ~((nb < 32 ? (1u << nb) : 0u) - 1u);
+    for (u32 p = 0; p < nb;) {
+      if (!((fits[5] >> p) & 1u)) {  // 33..64 records: the whole warp, two records per lane
+        tiny_sort64<KW>(j, __shfl_sync(kFull, c_begin, p), __shfl_sync(kFull, c_size, p),
+                        __shfl_sync(kFull, c_flags, p), slice, lane);
+        p++;
+        continue;
+      }
+      // widest grouping: G = 32 / w chunks starting at p, each of at most w records
+      u32 lw = 5;
+      for (u32 q = 1; q < 5; q++) {
+        const u32 G = 32u >> q;
+        const u32 span = G >= 32 ? kFull : ((1u << G) - 1u);
+        if (p + G <= 32 && ((fits[q] >> p) & span) == span) {
+          lw = q;
+          break;
+        }
+      }
+      const u32 w = 1u << lw, G = 32u >> lw;
+      const u32 g = lane >> lw, r = lane & (w - 1), c = p + g;
+      const u32 src_lane = c < 32 ? c : 31;  // (always c < 32: p + G <= 32, or G = 1)
+      const u64 begin = __shfl_sync(kFull, c_begin, src_lane);
+      const u32 size_c = __shfl_sync(kFull, c_size, src_lane), size = c < nb ? size_c : 0u;
+      const u32 flags = __shfl_sync(kFull, c_flags, src_lane);
+      const bool live = c < nb && r < size;
+      const u64* src = j.buf[(flags & kChSrcTmp) ? 1 : 0] + (begin + r) * RW;
+      u64* dst = j.buf[0] + (begin + r) * RW;
+      if (live)
+        for (u32 q = 0; q < RW; q++) mine[q] = src[q];
+      __syncwarp();
+      Key<KW> key;
+      u32 idx = r;
+      if (live) {
+        key.w[0] = mine[0] & j.keymask[0];
+        if (KW == 2) key.w[KW - 1] = mine[1] & j.keymask[1];
+      } else {
+#pragma unroll
+        for (int q = 0; q < KW; q++) key.w[q] = ~0ull;
+      }
+      for (u32 blk = 2; blk <= w; blk <<= 1) {
+        for (u32 d = blk >> 1; d > 0; d >>= 1) {
+          Key<KW> o;
+#pragma unroll
+          for (int q = 0; q < KW; q++) o.w[q] = __shfl_xor_sync(kFull, key.w[q], d);
+          const u32 oi = __shfl_xor_sync(kFull, idx, d);
+          const bool o_less = key_less<KW>(o, key) || (key_eq<KW>(o, key) && oi < idx);
+          // an ascending block keeps the smaller pair in its lower lane, a descending one the
+          // larger; the last merge of a group is ascending
+          const bool ascending = (r & blk) == 0, lower = (lane & d) == 0;
+          if (ascending == lower ? o_less : !o_less) {
+            key = o;
+            idx = oi;
+          }
+        }
+      }
+      // lane r writes its chunk's output record r: input record idx of the group (a chunk
+      // already in order keeps every record where it is, copied to `in` if it lives in tmp)
+      const bool copy_only = (flags & kChCopyOnly) != 0;
+      if (live && !(copy_only && (flags & kChSrcTmp) == 0)) {
+        const u64* sp = slice + (size_t)((g << lw) + (copy_only ? r : idx)) * RW;
+        if ((RW & 1) == 0) {
+          for (u32 q = 0; q < RW; q += 2)
+            __stcs(reinterpret_cast<ulonglong2*>(dst + q), *reinterpret_cast<const ulonglong2*>(sp + q));
+        } else {
+          for (u32 q = 0; q < RW; q++) __stcs(dst + q, sp[q]);
+        }
+      }
+      __syncwarp();  // the slice is reused by the next round
+      p += G;
+    }
+  }
+}
+
+int launch_tiny(const Job& j, u32 sms, cudaStream_t s) {
+  const size_t sm = (size_t)kTinyWarps * kTinyMax * j.RW * 8;
+  const u32 per_sm = (u32)std::max<size_t>(1, std::min<size_t>(8, (200 * 1024) / sm));
+  cudaError_t e;
+  if (j.KW == 1) {
+    cudaFuncSetAttribute(k_tiny<1>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
+    k_tiny<1><<<sms * per_sm, kTinyThreads, sm, s>>>(j);
+  } else {
+    cudaFuncSetAttribute(k_tiny<2>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
+    k_tiny<2><<<sms * per_sm, kTinyThreads, sm, s>>>(j);
+  }
+  e = cudaGetLastError();
   return e == cudaSuccess ? 1 : -1;
 }
 

@@ -35,7 +35,11 @@ enum : u32 { kErrTimeout = 1u, kErrOverflow = 2u, kErrInternal = 4u };
 enum : u32 { kBinRedo = 1u, kBinEqual = 2u };
 
 // Chunk flags
-enum : u32 { kChSrcTmp = 1u, kChCopyOnly = 2u, kChSegmented = 4u };
+enum : u32 { kChSrcTmp = 1u, kChCopyOnly = 2u };
+
+// Chunks of at most this many records are tiny: warps sort them with sorting networks in
+// registers (k_tiny) instead of a CTA.  They are listed from the top of the chunk array down.
+constexpr u32 kTinyMax = 64;
 
 // A bin handled by a multi-CTA distribution pass.
 struct Bin {
@@ -60,8 +64,6 @@ struct Chunk {
   u64 begin;
   u32 size;
   u32 flags;        // kChSrcTmp: records are in tmp (else in); kChCopyOnly: already sorted
-  u64 seg_first;    // segmented chunks: first segment (index into the offsets array)
-  u32 seg_count;
   u32 p;            // every key bit >= p is shared by the chunk (0: unknown, compute it)
   // A chunk packed from several sub-bins of one parent: they differ in the parent's digit
   // (key bits [p, p + pw)), whose values lie in [v0, v0 + 2^sb).  The chunk's first
@@ -84,6 +86,7 @@ struct Ctl {
   u32 cls_done;     // classify CTAs finished (the last one finalises the next list)
   u32 nredo;        // bins of this level whose digit moved after the count (recount needed)
   u64 nchunks, chunk_ticket;
+  u64 ntiny;        // tiny chunks, at chunks[cap_chunks - 1 - t] for t < ntiny
   u64 npieces, piece_ticket;
 };
 
@@ -293,6 +296,7 @@ int launch_hist(const Job& j, int level, int mode, cudaStream_t s);  // grid = j
 int launch_scatter(const Job& j, int level, u32 grid, cudaStream_t s);
 int launch_classify(const Job& j, int level, u32 grid, cudaStream_t s);
 int launch_chunks(const Job& j, u32 grid, cudaStream_t s);
+int launch_tiny(const Job& j, u32 sms, cudaStream_t s);
 int launch_copy(const Job& j, u32 grid, cudaStream_t s);
 int launch_read_counts(const Job& j, u64* d_counts, u32 W, cudaStream_t s);
 

@@ -136,7 +136,7 @@ __global__ void __launch_bounds__(kThreads) k_init_segments(Job j) {
   for (u64 base = blockIdx.x * (u64)kThreads; base < j.n_segs; base += (u64)gridDim.x * kThreads) {
     const u64 s = base + threadIdx.x;
     u64 a = 0, c = 0;
-    bool to_chunk = false, to_bin = false;
+    bool to_tiny = false, to_chunk = false, to_bin = false;
     if (s < j.n_segs) {
       const u64 e = j.seg_off[s + 1];
       a = j.seg_off[s];
@@ -144,26 +144,33 @@ __global__ void __launch_bounds__(kThreads) k_init_segments(Job j) {
         atomicOr(&ctl->err, kErrInternal);
       } else if (e > a + 1) {
         c = e - a;
-        to_chunk = c <= j.chunk_max;
-        to_bin = !to_chunk;
+        to_tiny = c <= kTinyMax;
+        to_chunk = !to_tiny && c <= j.chunk_max;
+        to_bin = c > j.chunk_max;
       }
     }
-    const u32 want = __ballot_sync(kFull, to_chunk);
-    u64 first = 0;
+    // one slot reservation per warp and list: chunks count up from 0, tiny chunks from the top
+    const u32 want = __ballot_sync(kFull, to_chunk), want_t = __ballot_sync(kFull, to_tiny);
+    u64 first = 0, first_t = 0;
     if (want) {
       const int leader = __ffs(want) - 1;
       if ((int)lane == leader) first = atomicAdd(&ctl->nchunks, (u64)__popc(want));
       first = __shfl_sync(kFull, first, leader);
     }
-    if (to_chunk) {
-      const u64 idx = first + __popc(want & lanemask_lt());
-      if (idx >= j.cap_chunks) {
+    if (want_t) {
+      const int leader = __ffs(want_t) - 1;
+      if ((int)lane == leader) first_t = atomicAdd(&ctl->ntiny, (u64)__popc(want_t));
+      first_t = __shfl_sync(kFull, first_t, leader);
+    }
+    if (to_chunk || to_tiny) {
+      const u64 t = to_tiny ? first_t + __popc(want_t & lanemask_lt()) : first + __popc(want & lanemask_lt());
+      if (t >= j.cap_chunks) {
         atomicOr(&ctl->err, kErrOverflow);
       } else {
         Chunk ch = {};
         ch.begin = a;
         ch.size = (u32)c;
-        j.chunks[idx] = ch;
+        j.chunks[to_tiny ? j.cap_chunks - 1 - t : t] = ch;
       }
     }
     if (!to_bin) continue;
@@ -796,6 +803,7 @@ __device__ __forceinline__ bool any_member(const u32* m, u32 a, u32 b) {
 constexpr int kClsThreads = 256;
 constexpr int kClsCtas = 4;  // per SM: a bin is a chain of dependent loads and barriers
 constexpr u16 kKeepChunk = 0x8000;
+constexpr u16 kTinyChunk = 0x8000;
 
 // Per bin of the level, for every sub-bin v of its digit: empty, one record (finished where
 // it is), 2..chunk_max records (sorted on chip), or more (a bin of the next level, whose
@@ -820,11 +828,12 @@ __global__ void __launch_bounds__(kClsThreads, kClsCtas) k_classify(Job j, int l
   __shared__ u16 vlast[kMaxD];          // chunk opened at v: its last non-empty sub-bin
   __shared__ u16 vnext[kMaxD];          // chunk opened at v: where the next opens | kKeepChunk
   __shared__ u16 pk[kMaxD];             // the bin's kept chunks: first sub-bin
+  __shared__ u16 pkr[kMaxD];            // ... and its place in its list | kTinyChunk
   __shared__ u32 m12[kMaxD / 32];       // sub-bins of 1..chunk_max records
   __shared__ u32 m2[kMaxD / 32];        // sub-bins of 2..chunk_max records
   __shared__ u32 scr[kClsThreads / 32];
-  __shared__ u32 s_npk;
-  __shared__ u64 s_base;
+  __shared__ u32 s_npk, s_nn, s_nt;
+  __shared__ u64 s_base, s_tbase;
   __shared__ int s_last;
   const int tid = threadIdx.x, lane = tid & 31;
   const u32 cm = j.chunk_max;
@@ -910,39 +919,47 @@ __global__ void __launch_bounds__(kClsThreads, kClsCtas) k_classify(Job j, int l
       vnext[v] = (u16)(next_member(m12, lo + 1, nd) | (keep ? kKeepChunk : 0u));
     }
     __syncthreads();
-    if (tid == 0) {
-      u32 npk = 0;
+    if (tid == 0) {  // (chunks of at most kTinyMax records go to the tiny list)
+      u32 npk = 0, nn = 0, nt = 0;
       for (u32 v = next_member(m12, 0, nd); v < nd;) {
         const u32 x = vnext[v];
-        if (x & kKeepChunk) pk[npk++] = (u16)v;
+        if (x & kKeepChunk) {
+          const u32 size = S[vlast[v]] - (v ? S[v - 1] : 0);
+          pk[npk] = (u16)v;
+          pkr[npk++] = (u16)(size <= kTinyMax ? (nt++ | kTinyChunk) : nn++);
+        }
         const u32 w = x & ~(u32)kKeepChunk;
         v = w > v ? w : nd;
       }
       s_npk = npk;
-      s_base = npk ? atomicAdd(&ctl->nchunks, (u64)npk) : 0;
+      s_nn = nn;
+      s_nt = nt;
+      s_base = nn ? atomicAdd(&ctl->nchunks, (u64)nn) : 0;
+      s_tbase = nt ? atomicAdd(&ctl->ntiny, (u64)nt) : 0;
     }
     __syncthreads();
     {
       const u32 npk = s_npk;
-      const u64 base = s_base;
-      if (base + npk > j.cap_chunks) {
-        if (tid == 0 && npk) atomicOr(&ctl->err, kErrOverflow);
-      } else {
-        for (u32 q = tid; q < npk; q += kClsThreads) {
-          const u32 vf = pk[q], vl = vlast[vf];
-          Chunk ch = {};
-          ch.begin = bin.begin + boff[vf];
-          ch.size = S[vl] - (vf ? S[vf - 1] : 0);
-          ch.flags = (p1 ? kChSrcTmp : 0u) | (any_member(m2, vf, vl) ? 0u : kChCopyOnly);
-          // one sub-bin shares every bit >= lo; several differ in the digit itself
-          ch.p = bin.lo;
-          ch.pw = (u16)bin.W;
-          ch.v0 = vf;
-          u32 sb = 0;
-          while ((1u << sb) < vl - vf + 1) sb++;
-          ch.sb = (u16)(vl == vf ? 0 : sb);
-          j.chunks[base + q] = ch;
-        }
+      const u64 base = s_base, tbase = s_tbase;
+      const bool ok = base + s_nn <= j.cap_chunks, ok_t = tbase + s_nt <= j.cap_chunks;
+      if (tid == 0 && !(ok && ok_t)) atomicOr(&ctl->err, kErrOverflow);
+      for (u32 q = tid; q < npk; q += kClsThreads) {
+        const u32 vf = pk[q], vl = vlast[vf], r = pkr[q];
+        const bool tiny = (r & kTinyChunk) != 0;
+        if (tiny ? !ok_t : !ok) continue;
+        Chunk ch = {};
+        ch.begin = bin.begin + boff[vf];
+        ch.size = S[vl] - (vf ? S[vf - 1] : 0);
+        ch.flags = (p1 ? kChSrcTmp : 0u) | (any_member(m2, vf, vl) ? 0u : kChCopyOnly);
+        // one sub-bin shares every bit >= lo; several differ in the digit itself
+        ch.p = bin.lo;
+        ch.pw = (u16)bin.W;
+        ch.v0 = vf;
+        u32 sb = 0;
+        while ((1u << sb) < vl - vf + 1) sb++;
+        ch.sb = (u16)(vl == vf ? 0 : sb);
+        const u32 rank = r & ~(u32)kTinyChunk;
+        j.chunks[tiny ? j.cap_chunks - 1 - (tbase + rank) : base + rank] = ch;
       }
     }
     __syncthreads();

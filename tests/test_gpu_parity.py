@@ -78,7 +78,7 @@ def test_sort_parity_uniform_1e6_r8():
 
 
 @pytest.mark.parametrize("kind", ["all_equal", "two_keys", "sorted", "reverse", "last_byte", "small_ints",
-                                  "few_distinct", "top_bit_only", "long_runs"])
+                                  "few_distinct", "top_bit_only", "long_runs", "heavy_gaps"])
 def test_sort_parity_degenerate(kind):
     rng = np.random.default_rng(11)
     n, R, K = 400_000, 16, 8
@@ -102,6 +102,13 @@ def test_sort_parity_degenerate(kind):
         keys[:] = (rng.integers(0, 2, n).astype(np.uint64) << np.uint64(63))
     elif kind == "long_runs":
         keys[:] = np.repeat(rng.integers(0, 1 << 64, n // 5000 + 1, dtype=np.uint64), 5000)[:n]
+    elif kind == "heavy_gaps":
+        # 8 heavy top digits (large sub-bins, the next level) with a few hundred records spread
+        # between them: the runs of small sub-bins between two heavy ones pack into tiny chunks
+        top = rng.choice(512, 8, replace=False).astype(np.uint64)
+        keys[:] = (top[rng.integers(0, 8, n)] << np.uint64(55)) | rng.integers(0, 1 << 55, n).astype(np.uint64)
+        few = rng.random(n) < 0.001
+        keys[few] = rng.integers(0, 1 << 64, int(few.sum()), dtype=np.uint64)
     a[:, :8] = keys.view(np.uint8).reshape(n, 8)
     np.testing.assert_array_equal(gsort(a, K), oracle.sort(a, K))
 
@@ -136,6 +143,26 @@ def test_segmented_parity():
     torch.cuda.synchronize()
     rg.check_status()
     np.testing.assert_array_equal(from_dev(t), oracle.sort_segmented(a, off, 8))
+
+
+@pytest.mark.parametrize("R,K", [(8, 8), (8, 3), (16, 8), (16, 16), (24, 5), (40, 13), (64, 16), (256, 9)])
+def test_segmented_tiny_parity(R, K):
+    """Many segments of 0..80 records: tiny ones (2..64) are sorted by warps with sorting
+    networks (several chunks of up to 32 records per warp, or one of 33..64 records with two
+    per lane), 65..80 by the CTA sorter; a few large ones keep the level path busy.  Few
+    distinct keys, so equal keys must keep their input order."""
+    rng = np.random.default_rng(R * 13 + K)
+    sizes = rng.integers(0, 81, 4000).astype(np.uint64)
+    sizes[::97] = rng.integers(2000, 30_000, len(sizes[::97]))
+    sizes[:80] = np.arange(80)  # every tiny size, in order
+    off = np.concatenate([[0], np.cumsum(sizes)]).astype(np.uint64)
+    n = int(off[-1])
+    a = rand(rng, n, R, K, distinct=7)
+    t = to_dev(a)
+    rg.sort_segmented(t, torch.from_numpy(off.astype(np.int64)).cuda(), K, total=n)
+    torch.cuda.synchronize()
+    rg.check_status()
+    np.testing.assert_array_equal(from_dev(t), oracle.sort_segmented(a, off, K))
 
 
 def test_segmented_matches_plain_alone():

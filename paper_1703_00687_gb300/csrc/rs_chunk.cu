@@ -16,6 +16,9 @@
 //     back in input order (ranks of its input positions, from a bitmap of them);
 //   * a chunk of at most kEsMax records is one enumeration sort, without a distribution.
 // The result is therefore the stable order, and the whole sorter is stable.
+//
+// Chunks of at most kTinyMax records are kept in a list of their own and sorted by k_tiny:
+// warps, not CTAs, with bitonic sorting networks over lane shuffles (several chunks per warp).
 #include <algorithm>
 
 #include "rs_internal.cuh"

@@ -806,7 +806,8 @@ def main():
             times.append(time.perf_counter() - t0)
         et = max_over_ranks(sum(times), dist, dev)
         e2e = {"value": n * world * len(times) / et, "unit": "records/s", "h2d_bytes_per_step": n * R,
-               "d2h_bytes_per_step": n * R, "ms_per_step": 1e3 * et / len(times), "api": "sort_host (pinned)"}
+               "d2h_bytes_per_step": n * R, "ms_per_step": 1e3 * et / len(times),
+               "api": "radix_sort_host (one C-ABI call: H2D, sort, D2H; pinned host buffers)"}
 
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu:

@@ -75,6 +75,23 @@ rs_status radix_sort(void *in, void *tmp, uint64_t n, uint32_t rec_size, uint32_
                      rs_stream_t stream);
 
 /*
+ * Sort n records that live in HOST memory: copy them to the device, sort, copy them back.
+ *   h_in      HOST pointer, n * rec_size bytes: the records (read).
+ *   h_out     HOST pointer, n * rec_size bytes: receives the sorted records; may equal h_in.
+ *             Page-locked (pinned) host memory makes both copies asynchronous; with pageable
+ *             memory the CUDA runtime stages them and the call may return later.
+ *   d_buf     DEVICE pointer, n * rec_size bytes, 16-byte aligned: holds the records on the
+ *             device (sorted there, then copied out).
+ *   d_tmp     DEVICE pointer, n * rec_size bytes, 16-byte aligned, not overlapping d_buf.
+ *   n, rec_size, key_size, stream: as for radix_sort.  The copies and the sort are enqueued on
+ *   `stream`; h_out holds the result once the stream has reached this point.  The caller
+ *   owns all four buffers.  Errors as for radix_sort, plus RS_ERR_INVALID_ARG for a null
+ *   host pointer with n > 0 and RS_ERR_CUDA if a copy cannot be enqueued.
+ */
+rs_status radix_sort_host(const void *h_in, void *h_out, void *d_buf, void *d_tmp, uint64_t n, uint32_t rec_size,
+                          uint32_t key_size, rs_stream_t stream);
+
+/*
  * Sort many independent instances in one call: segment s is records
  * [seg_offsets[s], seg_offsets[s+1]) of `in`, sorted on its own, in place.
  *   seg_offsets  DEVICE pointer to n_segs + 1 uint64 values: non-decreasing, [0] = 0,

@@ -55,11 +55,7 @@ def sort(records, key_size: int, tmp=None, stream=None):
     """
     torch = _torch()
     if records.device.type == "cpu":
-        dev = torch.empty_like(records, device="cuda")
-        dev.copy_(records, non_blocking=True)
-        sort(dev, key_size, tmp=tmp, stream=stream)
-        records.copy_(dev, non_blocking=False)
-        return records
+        return sort_host(records, key_size, d_tmp=tmp, stream=stream)
     _need_cuda(records, "records")
     n = records.shape[0]
     if tmp is None:
@@ -71,23 +67,32 @@ def sort(records, key_size: int, tmp=None, stream=None):
 
 
 def sort_host(h_in, key_size: int, h_out=None, d_buf=None, d_tmp=None, stream=None):
-    """Sort host records through the GPU: copy ``h_in`` to the device, sort, copy back.
+    """Sort host records through the GPU with one ``radix_sort_host`` call: copy ``h_in`` to
+    the device, sort, copy back, all on ``stream``.
 
     The result goes to ``h_out`` (default: ``h_in`` itself).  ``d_buf``/``d_tmp``: optional
     device buffers of the same shape, reused across calls.  Pinned host tensors make the
     copies asynchronous.  Returns after the result is on the host.
     """
     torch = _torch()
+    if h_in.is_cuda or (h_out is not None and h_out.is_cuda):
+        raise ValueError("sort_host takes host tensors")
+    if not h_in.is_contiguous() or (h_out is not None and (not h_out.is_contiguous() or h_out.shape != h_in.shape)):
+        raise ValueError("host tensors must be contiguous and of the same shape")
     if d_buf is None:
         d_buf = torch.empty_like(h_in, device="cuda")
     if d_tmp is None:
         d_tmp = torch.empty_like(d_buf)
+    _need_cuda(d_buf, "d_buf")
+    _need_cuda(d_tmp, "d_tmp")
+    nbytes = h_in.numel() * h_in.element_size()
+    if d_buf.numel() * d_buf.element_size() < nbytes or d_tmp.numel() * d_tmp.element_size() < nbytes:
+        raise ValueError("d_buf and d_tmp must hold the records")
+    out = h_in if h_out is None else h_out
     s = torch.cuda.current_stream() if stream is None else stream
-    with torch.cuda.stream(s):
-        d_buf.copy_(h_in, non_blocking=True)
-        sort(d_buf, key_size, tmp=d_tmp, stream=s)
-        out = h_in if h_out is None else h_out
-        out.copy_(d_buf, non_blocking=True)
+    n = h_in.shape[0] if h_in.dim() > 0 else 0
+    check(lib().radix_sort_host(h_in.data_ptr(), out.data_ptr(), d_buf.data_ptr(), d_tmp.data_ptr(), n,
+                                _rec_size(h_in), key_size, _stream(s)), "radix_sort_host")
     s.synchronize()
     return out
 

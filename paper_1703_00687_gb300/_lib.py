@@ -35,6 +35,7 @@ KERNEL_NAMES = {0: "init", 1: "hist", 2: "hist_redo", 3: "scatter", 4: "classify
 
 SIGNATURES = {
     "radix_sort": (_i32, [_vp, _vp, _u64, _u32, _u32, _vp]),
+    "radix_sort_host": (_i32, [_vp, _vp, _vp, _vp, _u64, _u32, _u32, _vp]),
     "radix_sort_segmented": (_i32, [_vp, _vp, _vp, _u64, _u64, _u32, _u32, _vp]),
     "radix_partition": (_i32, [_vp, _vp, _u64, _u32, _u32, _u32, _u32, _vp]),
     "radix_histogram": (_i32, [_vp, _u64, _u32, _u32, _u32, _u32, _vp, _vp]),

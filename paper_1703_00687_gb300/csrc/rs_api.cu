@@ -439,6 +439,22 @@ rs_status radix_sort(void* in, void* tmp, uint64_t n, uint32_t rec_size, uint32_
   return run_levels(st, s);
 }
 
+rs_status radix_sort_host(const void* h_in, void* h_out, void* d_buf, void* d_tmp, uint64_t n, uint32_t rec_size,
+                          uint32_t key_size, rs_stream_t stream) {
+  rs_status r = validate_layout(rec_size, key_size);
+  if (r != RS_OK) return r;
+  if (n > UINT64_MAX / rec_size) return RS_ERR_TOO_LARGE;
+  if (n == 0) return RS_OK;
+  if (!h_in || !h_out) return RS_ERR_INVALID_ARG;
+  if ((r = validate_buffers(d_buf, d_tmp, n, rec_size)) != RS_OK) return r;
+  const size_t bytes = (size_t)(n * rec_size);
+  cudaStream_t s = (cudaStream_t)stream;
+  if (cudaMemcpyAsync(d_buf, h_in, bytes, cudaMemcpyHostToDevice, s) != cudaSuccess) return RS_ERR_CUDA;
+  if ((r = radix_sort(d_buf, d_tmp, n, rec_size, key_size, stream)) != RS_OK) return r;
+  if (cudaMemcpyAsync(h_out, d_buf, bytes, cudaMemcpyDeviceToHost, s) != cudaSuccess) return RS_ERR_CUDA;
+  return RS_OK;
+}
+
 rs_status radix_sort_segmented(void* in, void* tmp, const uint64_t* seg_offsets, uint64_t n_segs, uint64_t total,
                                uint32_t rec_size, uint32_t key_size, rs_stream_t stream) {
   rs_status r = validate_layout(rec_size, key_size);

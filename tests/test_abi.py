@@ -68,6 +68,17 @@ def test_buffer_validation():
     assert L.radix_sort_segmented(A, B, None, 0, 0, 16, 8, None) == 0
 
 
+def test_host_entry_validation():
+    L = rg.lib()
+    H = ctypes.c_void_p(1 << 20)  # never dereferenced: every case below fails validation first
+    assert L.radix_sort_host(None, H, A, B, 100, 16, 8, None) == 1       # null host input
+    assert L.radix_sort_host(H, None, A, B, 100, 16, 8, None) == 1       # null host output
+    assert L.radix_sort_host(H, H, A + 8, B, 100, 16, 8, None) == 2      # misaligned device buffer
+    assert L.radix_sort_host(H, H, A, A + 16 * 50, 100, 16, 8, None) == 3  # device buffers overlap
+    assert L.radix_sort_host(H, H, A, B, 100, 12, 8, None) == 1          # rec_size not a multiple of 8
+    assert L.radix_sort_host(None, None, None, None, 0, 16, 8, None) == 0  # nothing to do
+
+
 def test_digit_validation():
     L = rg.lib()
     assert L.radix_partition(A, B, 100, 16, 8, 0, 0, None) == 1     # width 0

@@ -199,6 +199,20 @@ def test_host_tensor_roundtrip():
     np.testing.assert_array_equal(t.numpy(), oracle.sort(a, 8))
 
 
+@pytest.mark.parametrize("n,R,K", [(300_007, 24, 16), (1000, 8, 8), (5, 16, 8)])
+def test_sort_host_entry(n, R, K):
+    """radix_sort_host: pinned input, a separate pinned output, caller's device buffers."""
+    rng = np.random.default_rng(n)
+    a = rand(rng, n, R, K, distinct=n // 2 + 1)
+    h_in = torch.from_numpy(a.copy()).pin_memory()
+    h_out = torch.empty_like(h_in).pin_memory()
+    d_buf = torch.empty(h_in.shape, dtype=h_in.dtype, device="cuda")
+    d_tmp = torch.empty_like(d_buf)
+    rg.sort_host(h_in, K, h_out=h_out, d_buf=d_buf, d_tmp=d_tmp)
+    np.testing.assert_array_equal(h_out.numpy(), oracle.sort(a, K))
+    np.testing.assert_array_equal(h_in.numpy(), a)  # the input is only read
+
+
 # ------------------------------------------------ run-length counting after the sort (k-mer counting)
 @pytest.mark.parametrize("n,R,K,distinct", [(300_007, 24, 16, 5000), (200_000, 16, 8, 70_000), (9_000, 8, 3, 10),
                                             (50_000, 24, 16, 1), (4097, 16, 8, None)])

@@ -32,7 +32,7 @@ constexpr u32 kFull = 0xffffffffu;
 enum : u32 { kErrTimeout = 1u, kErrOverflow = 2u, kErrInternal = 4u };
 
 // Bin flags
-enum : u32 { kBinRedo = 1u, kBinEqual = 2u };
+enum : u32 { kBinRedo = 1u, kBinEqual = 2u, kBinDom = 4u };
 
 // Chunk flags
 enum : u32 { kChSrcTmp = 1u, kChCopyOnly = 2u };
@@ -46,9 +46,10 @@ struct Bin {
   u64 begin;        // first record
   u64 size;         // records
   u64 tile_start;   // number of the bin's first tile within its level
-  u64 base_off;     // first of its 2^W entries in the level's bucket-base pool
+  u64 base_off;     // first of its 2^bucket_bits entries in the level's bucket-base pool
   u64 kand[2];      // AND / OR of the bin's keys, gathered by the histogram pass: they tell
   u64 kor[2];       // whether the digit starts at the highest differing bit, or all keys are equal
+  u64 dom[2];       // kBinDom: the key that holds most of the bin (its bucket is finished)
   u32 lo, W;        // the digit is key bits [lo, lo + W)
   u32 parity;       // 0: the bin's records are in `in`; 1: in `tmp`
   u32 flags;
@@ -141,6 +142,14 @@ __device__ __forceinline__ Key<KW> load_key(const u64* rec, const Job& j) {
   return k;
 }
 
+// Buckets of a bin.  A plain bin has one bucket per digit value (key bits [lo, lo + W)).  A bin
+// that one key K dominates (kBinDom; seen in a sample when the bin was formed) splits K's
+// digit dK in three -- keys below K, K itself, keys above K -- so that K's records are
+// finished by this pass instead of being moved again at every later level: digits below dK
+// keep their number, dK becomes dK (below K), dK + 1 (K) and dK + 2 (above K), digits above
+// dK move up by two.  Its bucket numbers fit W + 1 bits.
+__host__ __device__ inline u32 bucket_bits(u32 W, u32 flags) { return W + ((flags & kBinDom) ? 1u : 0u); }
+
 // Digit = key bits [lo, lo + W), W <= 16.
 template <int KW>
 __device__ __forceinline__ u32 digit_of(const Key<KW>& k, u32 lo, u32 W) {
@@ -170,6 +179,16 @@ __device__ __forceinline__ bool key_eq(const Key<KW>& a, const Key<KW>& b) {
   bool e = a.w[0] == b.w[0];
   if (KW == 2) e = e && a.w[KW - 1] == b.w[KW - 1];
   return e;
+}
+
+// Bucket of key k in a bin with digit [lo, lo + W): the digit, or for a dominated bin (dom)
+// the three-way split of K's digit dK (see bucket_bits).
+template <int KW>
+__device__ __forceinline__ u32 bucket_of(const Key<KW>& k, u32 lo, u32 W, bool dom, const Key<KW>& K, u32 dK) {
+  const u32 d = digit_of<KW>(k, lo, W);
+  if (!dom) return d;
+  if (d != dK) return d < dK ? d : d + 2;
+  return key_less<KW>(k, K) ? dK : key_eq<KW>(k, K) ? dK + 1 : dK + 2;
 }
 
 // Position of the highest set bit plus one (0 if none) over a KW-word value.

@@ -214,7 +214,7 @@ __device__ void finish_bin(const Job& j, int L, u64 b, int mode) {
   Ctl* ctl = j.ctl;
   Bin* bp = &j.bins[L][b];
   const u32 W = bp->W;
-  const u32 nd = 1u << W;
+  const u32 nd = 1u << bucket_bits(W, bp->flags);  // buckets (the digit moves, the split stays)
   const u64 size = bp->size;
   u64* base = j.base[L] + bp->base_off;
   if (threadIdx.x == 0) {
@@ -320,7 +320,7 @@ __global__ void __launch_bounds__(kThreads, 2) k_hist(Job j, int level, int mode
   auto flush = [&](u64 b) {
     __syncthreads();
     const Bin* bb = &bins[b];
-    const u32 nd = 1u << bb->W;
+    const u32 nd = 1u << bucket_bits(bb->W, bb->flags);
     const u64 bo = bb->base_off;
     const u64 sid = lane_id + b;  // segment of (lane, bin)
     if (sid >= j.cap_seg) {    // cannot happen: lanes + bins segments are allocated
@@ -383,6 +383,7 @@ __global__ void __launch_bounds__(kThreads, 2) k_hist(Job j, int level, int mode
   struct TileRef {
     u64 b;
     u32 cnt, lo, W, skip;
+    bool dom;  // kBinDom: buckets split around the dominant key
   };
   u64 walk = find_bin(bins, nb, t0);
   // locate tile t and start copying its keys into buffer `buf`
@@ -394,6 +395,7 @@ __global__ void __launch_bounds__(kThreads, 2) k_hist(Job j, int level, int mode
     tr.skip = (mode == 1 && !(bp->flags & kBinRedo)) ? 1u : 0u;
     tr.lo = bp->lo;
     tr.W = bp->W;
+    tr.dom = (bp->flags & kBinDom) != 0;
     const u64 tib = t - bp->tile_start;
     const u64 r0 = tib * T;
     tr.cnt = (u32)min((u64)T, bp->size - r0);
@@ -428,18 +430,29 @@ __global__ void __launch_bounds__(kThreads, 2) k_hist(Job j, int level, int mode
     }
     if (!tc.skip) {
       const u64* kb = kbuf + (size_t)buf * T * KW;
-      for (u32 r = tid; r < tc.cnt; r += kThreads) {
-        Key<KW> k;
+      auto count = [&](auto&& bucket) {
+        for (u32 r = tid; r < tc.cnt; r += kThreads) {
+          Key<KW> k;
 #pragma unroll
-        for (int q = 0; q < KW; q++) k.w[q] = kb[KW * r + q] & j.keymask[q];
-        atomicAdd(&my_hist[digit_of<KW>(k, tc.lo, tc.W)], 1u);
-        if (want_masks) {
+          for (int q = 0; q < KW; q++) k.w[q] = kb[KW * r + q] & j.keymask[q];
+          atomicAdd(&my_hist[bucket(k)], 1u);
+          if (want_masks) {
 #pragma unroll
-          for (int q = 0; q < KW; q++) {
-            kand[q] &= k.w[q];
-            kor[q] |= k.w[q];
+            for (int q = 0; q < KW; q++) {
+              kand[q] &= k.w[q];
+              kor[q] |= k.w[q];
+            }
           }
         }
+      };
+      if (!tc.dom) {
+        count([&](const Key<KW>& k) { return digit_of<KW>(k, tc.lo, tc.W); });
+      } else {  // (rare: a bin that a sample showed to be mostly one key)
+        Key<KW> K;
+#pragma unroll
+        for (int q = 0; q < KW; q++) K.w[q] = bins[tc.b].dom[q];
+        const u32 dK = digit_of<KW>(K, tc.lo, tc.W);
+        count([&](const Key<KW>& k) { return bucket_of<KW>(k, tc.lo, tc.W, true, K, dK); });
       }
       counted++;
     }
@@ -551,11 +564,28 @@ __global__ void __launch_bounds__(kSThreads, 2) k_scatter(Job j, int level) {
     for (u64 t = t0; t < t1; t++) {
       while (b + 1 < nb && bins[b + 1].tile_start <= t) b++;
       const Bin* bp = &bins[b];
-      const u32 lo = bp->lo, W = bp->W, nd = 1u << W;
-    // per-warp counters with a row stride of this bin's digit count (every tile zeroes the
-    // rows it used, so the rows of a narrower or wider digit start at zero too)
-    const u32 WS = nd < 2 ? 2 : nd;
-    u16* wh = whist + warp * WS;
+      const u32 lo = bp->lo, W = bp->W, BW = bucket_bits(W, bp->flags), nd = 1u << BW;
+      const bool dom = (bp->flags & kBinDom) != 0;
+      Key<KW> K = {};
+      u32 dK = 0;
+      if (dom) {
+#pragma unroll
+        for (int q = 0; q < KW; q++) K.w[q] = bp->dom[q];
+        dK = digit_of<KW>(K, lo, W);
+      }
+      // bucket of a staged record (a digit window never reaches past the key, so only the
+      // comparisons with a dominant key need the key mask)
+      auto bucket = [&](const u64* rec) -> u32 {
+        if (!dom) return staged_digit<KW>(rec, lo, W);
+        Key<KW> k;
+#pragma unroll
+        for (int q = 0; q < KW; q++) k.w[q] = rec[q] & j.keymask[q];
+        return bucket_of<KW>(k, lo, W, true, K, dK);
+      };
+      // per-warp counters with a row stride of this bin's bucket count (every tile zeroes the
+      // rows it used, so the rows of a narrower or wider digit start at zero too)
+      const u32 WS = nd < 2 ? 2 : nd;
+      u16* wh = whist + warp * WS;
       const u64 begin = bp->begin, size = bp->size;
       const u64 tib = t - bp->tile_start;
       const u32 parity = bp->parity;
@@ -586,10 +616,18 @@ __global__ void __launch_bounds__(kSThreads, 2) k_scatter(Job j, int level) {
       if (cnt == T) {
         // first every item's digit and peers (independent of each other), then the counters
         u32 dg[IT], pr[IT];
+        if (!dom) {  // (the two loops differ in the bucket function only)
 #pragma unroll
-        for (int it = 0; it < IT; it++) {
-          dg[it] = staged_digit<KW>(stage + (u64)(warp * PW + it * 32 + lane) * RW, lo, W);
-          pr[it] = peers_of(dg[it], W, true);
+          for (int it = 0; it < IT; it++) {
+            dg[it] = staged_digit<KW>(stage + (u64)(warp * PW + it * 32 + lane) * RW, lo, W);
+            pr[it] = peers_of(dg[it], W, true);
+          }
+        } else {
+#pragma unroll
+          for (int it = 0; it < IT; it++) {
+            dg[it] = bucket(stage + (u64)(warp * PW + it * 32 + lane) * RW);
+            pr[it] = peers_of(dg[it], BW, true);
+          }
         }
 #pragma unroll
         for (int it = 0; it < IT; it++) {
@@ -607,8 +645,8 @@ __global__ void __launch_bounds__(kSThreads, 2) k_scatter(Job j, int level) {
           const u32 r = warp * PW + it * 32 + lane;
           const bool valid = r < cnt;
           u32 d = 0;
-          if (valid) d = staged_digit<KW>(stage + (u64)r * RW, lo, W);
-          const u32 peers = peers_of(d, W, valid);
+          if (valid) d = bucket(stage + (u64)r * RW);
+          const u32 peers = peers_of(d, BW, valid);
           const u32 before = __popc(peers & ltmask);
           u32 old = 0;
           if (valid) old = wh[d];
@@ -732,22 +770,31 @@ __global__ void __launch_bounds__(kSThreads, 2) k_scatter(Job j, int level) {
 }
 
 // -------------------------------------------------------------------- classify
-// Highest differing key bit + 1 over 32 records spread over a sub-bin (the sample tells where
-// the sub-bin's next digit probably starts; the next histogram pass checks, and moves it).
+// 32 records spread over a sub-bin: their highest differing key bit + 1 (where the sub-bin's
+// next digit probably starts; the next histogram pass checks, and moves it), and the key that
+// most of them share (of the first and the middle sample), with how many share it.
+constexpr u32 kSamples = 32;
+constexpr u32 kDomSamples = 16;  // samples sharing one key that make a bin dominated (half)
+
 template <int KW>
-__device__ u32 sample_top_bit(const Job& j, const u64* rec, u64 c) {
+__device__ u32 sample_sub_bin(const Job& j, const u64* rec, u64 c, Key<KW>* kdom, u32* ndom) {
+  const Key<KW> c0 = load_key<KW>(rec, j), c1 = load_key<KW>(rec + (c * (kSamples / 2) / kSamples) * j.RW, j);
   u64 a[2] = {~0ull, ~0ull}, o[2] = {0, 0};
-  const int ns = 32;
+  u32 n0 = 0, n1 = 0;
 #pragma unroll(8 / KW)
-  for (int i = 0; i < ns; i++) {
-    const u64 r = (c * (u64)i) / ns;
+  for (u32 i = 0; i < kSamples; i++) {
+    const u64 r = (c * (u64)i) / kSamples;
     const Key<KW> k = load_key<KW>(rec + r * j.RW, j);
 #pragma unroll
     for (int q = 0; q < KW; q++) {
       a[q] &= k.w[q];
       o[q] |= k.w[q];
     }
+    n0 += key_eq<KW>(k, c0);
+    n1 += key_eq<KW>(k, c1);
   }
+  *kdom = n1 > n0 ? c1 : c0;
+  *ndom = n1 > n0 ? n1 : n0;
   return top_bit_plus1(a[0] ^ o[0], KW == 2 ? a[1] ^ o[1] : 0);
 }
 
@@ -843,9 +890,17 @@ __global__ void __launch_bounds__(kClsThreads, kClsCtas) k_classify(Job j, int l
       if (tid == 0 && bin.parity) push_pieces(j, bin.begin, bin.size);
       continue;
     }
-    const u32 nd = 1u << bin.W;
+    const u32 nd = 1u << bucket_bits(bin.W, bin.flags);
     const u32 p1 = bin.parity ^ 1;
     const u64* bbase = j.base[L] + bin.base_off;
+    const bool dom = (bin.flags & kBinDom) != 0;
+    u32 vdom = nd;  // the dominant key's bucket: finished here
+    if (dom) {
+      Key<KW> K;
+#pragma unroll
+      for (int q = 0; q < KW; q++) K.w[q] = bin.dom[q];
+      vdom = digit_of<KW>(K, bin.lo, bin.W) + 1;
+    }
     for (u32 v0 = tid & ~31u; v0 < nd; v0 += kClsThreads) {
       const u32 v = v0 + lane;
       u32 k = 0;
@@ -860,16 +915,30 @@ __global__ void __launch_bounds__(kClsThreads, kClsCtas) k_classify(Job j, int l
         boff[v] = bv;
         k = c == 0 ? 0 : c == 1 ? 1 : c <= cm ? 2 : 3;
         S[v] = k == 3 ? cm + 1 : (u32)c;
+        if (v == vdom) {  // all the dominant key: finished (copied back if it lives in tmp); no
+          k = 0;          // chunk may reach across it
+          S[v] = c ? cm + 1 : 0;
+          if (c && p1) push_pieces(j, bin.begin + bv, c);
+        }
         if (k == 3) {
           const u64 rb = bin.begin + bv;
           // every key bit >= bin.lo is shared by the sub-bin; guess where its next digit
-          // starts from a sample
-          u32 p = sample_top_bit<KW>(j, j.buf[p1] + rb * j.RW, c);
+          // starts from a sample, and whether one key holds most of it
+          Key<KW> K2;
+          u32 ndom;
+          u32 p = sample_sub_bin<KW>(j, j.buf[p1] + rb * j.RW, c, &K2, &ndom);
           if (p == 0 || p > bin.lo) p = bin.lo;
           if (p == 0) p = 1;
           u32 nlo, nW;
           plan_digit(c, p, cm, j.wmax, &nlo, &nW);
-          const u32 nnd = 1u << nW;
+          // a dominated bin takes one digit bit less, so its 2^(W+1) buckets need no more room
+          // than a plain bin's (the other keys are at most half of it)
+          const bool dom2 = ndom >= kDomSamples && nW >= 2;
+          if (dom2) {
+            nW -= 1;
+            nlo += 1;
+          }
+          const u32 nnd = 1u << bucket_bits(nW, dom2 ? kBinDom : 0u);
           const u64 idx = atomicAdd(&ctl->nbins[N], 1ull);
           const u64 bo = atomicAdd(&ctl->base_used[N], (u64)nnd);
           if (idx >= j.cap_bins || bo + nnd > j.cap_base) {
@@ -883,6 +952,11 @@ __global__ void __launch_bounds__(kClsThreads, kClsCtas) k_classify(Job j, int l
             nbn.lo = nlo;
             nbn.W = nW;
             nbn.parity = p1;
+            if (dom2) {
+              nbn.flags = kBinDom;
+#pragma unroll
+              for (int q = 0; q < KW; q++) nbn.dom[q] = K2.w[q];
+            }
             j.bins[N][idx] = nbn;
             for (u32 q = 0; q < nnd; q++) j.base[N][bo + q] = 0;
           }
@@ -951,13 +1025,16 @@ __global__ void __launch_bounds__(kClsThreads, kClsCtas) k_classify(Job j, int l
         ch.begin = bin.begin + boff[vf];
         ch.size = S[vl] - (vf ? S[vf - 1] : 0);
         ch.flags = (p1 ? kChSrcTmp : 0u) | (any_member(m2, vf, vl) ? 0u : kChCopyOnly);
-        // one sub-bin shares every bit >= lo; several differ in the digit itself
-        ch.p = bin.lo;
-        ch.pw = (u16)bin.W;
-        ch.v0 = vf;
-        u32 sb = 0;
-        while ((1u << sb) < vl - vf + 1) sb++;
-        ch.sb = (u16)(vl == vf ? 0 : sb);
+        // one sub-bin shares every bit >= lo; several differ in the digit itself (the bucket
+        // numbers of a dominated bin are not key bits: its chunks find their shared bits)
+        if (!dom) {
+          ch.p = bin.lo;
+          ch.pw = (u16)bin.W;
+          ch.v0 = vf;
+          u32 sb = 0;
+          while ((1u << sb) < vl - vf + 1) sb++;
+          ch.sb = (u16)(vl == vf ? 0 : sb);
+        }
         const u32 rank = r & ~(u32)kTinyChunk;
         j.chunks[tiny ? j.cap_chunks - 1 - (tbase + rank) : base + rank] = ch;
       }

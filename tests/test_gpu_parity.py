@@ -113,6 +113,51 @@ def test_sort_parity_degenerate(kind):
     np.testing.assert_array_equal(gsort(a, K), oracle.sort(a, K))
 
 
+@pytest.mark.parametrize("R,K,pattern", [(16, 8, "90"), (16, 8, "55"), (16, 8, "two"), (16, 8, "zero"),
+                                         (16, 8, "ones"), (24, 16, "90"), (24, 16, "ones"), (16, 5, "90"),
+                                         (8, 8, "97"), (64, 16, "two")])
+def test_sort_parity_dominant_key(R, K, pattern):
+    """Bins that one key dominates: the sample at bin formation flags them, and the next pass
+    splits that key's digit in three (below / equal / above) and finishes the equal part.
+    Payloads are random, so the equal keys must come out in input order."""
+    rng = np.random.default_rng(R * 7 + K + len(pattern))
+    n = 600_000
+    a = rand(rng, n, R, K)
+    keys = a[:, :K].copy()
+    def put(mask, key_bytes):
+        keys[mask] = key_bytes
+    u = rng.random(n)
+    if pattern in ("90", "55", "97"):
+        frac = int(pattern) / 100
+        put(u < frac, rng.integers(0, 256, K, dtype=np.uint8))
+    elif pattern == "two":
+        put(u < 0.45, rng.integers(0, 256, K, dtype=np.uint8))
+        put((u >= 0.45) & (u < 0.9), rng.integers(0, 256, K, dtype=np.uint8))
+    elif pattern == "zero":  # the smallest key: its digit is 0 at every level
+        put(u < 0.8, np.zeros(K, dtype=np.uint8))
+    elif pattern == "ones":  # the largest key: its digit is the last one
+        put(u < 0.8, np.full(K, 255, dtype=np.uint8))
+    a[:, :K] = keys
+    np.testing.assert_array_equal(gsort(a, K), oracle.sort(a, K))
+
+
+def test_segmented_dominant_segments():
+    rng = np.random.default_rng(77)
+    sizes = np.array([300_000, 50, 120_000, 7, 80_000, 0, 200_000], dtype=np.uint64)
+    off = np.concatenate([[0], np.cumsum(sizes)]).astype(np.uint64)
+    n = int(off[-1])
+    a = rand(rng, n, 16, 8)
+    for s in range(len(sizes)):  # every segment mostly one key of its own
+        lo, hi = int(off[s]), int(off[s + 1])
+        m = rng.random(hi - lo) < 0.85
+        a[lo:hi][m, :8] = rng.integers(0, 256, 8, dtype=np.uint8)
+    t = to_dev(a)
+    rg.sort_segmented(t, torch.from_numpy(off.astype(np.int64)).cuda(), 8, total=n)
+    torch.cuda.synchronize()
+    rg.check_status()
+    np.testing.assert_array_equal(from_dev(t), oracle.sort_segmented(a, off, 8))
+
+
 def test_sort_parity_zipf():
     a = wl.zipf(1_500_000, 16, seed=3)
     np.testing.assert_array_equal(gsort(a, 8), oracle.sort(a, 8))

@@ -13,7 +13,12 @@
 //               CTA of a bin also turns every lane's counts into that lane's run starts.
 //   k_scatter   tile-wise stable scatter, lane by lane: a tile's destinations follow from its
 //               lane's run starts and the lane's earlier tiles (no CTA waits for another).
-//   k_classify  sub-bin classification, chunk packing, the next level's bin list.
+//   k_classify  sub-bin classification, chunk packing (chunks of at most kTinyMax records go
+//               to the tiny list), the next level's bin list.
+//
+// A bin that a sample showed to be mostly one key (kBinDom) is counted and scattered with
+// that key's digit split in three (below, equal, above; see bucket_of), and classify
+// finishes the equal part at once: heavy keys are not moved again at later levels.
 #include "rs_internal.cuh"
 
 namespace rsg {

@@ -295,11 +295,12 @@ static int timed(u32 kernel, u32 level, cudaStream_t s, F&& launch) {
 }
 
 // Levels 0..K-1 of distribution passes, then the on-chip sorts and the copy-back.
-static rs_status run_levels(const Setup& st, cudaStream_t s) {
+// levels = 0 when no bin can exceed the on-chip limit (then only chunks exist).
+static rs_status run_levels(const Setup& st, cudaStream_t s, bool levels_needed = true) {
   const Job& j = st.j;
   const u32 gs = (u32)st.sms * (u32)scatter_ctas_per_sm(j);
   const u32 gc = (u32)st.sms * (u32)classify_ctas_per_sm();
-  const int levels = (int)j.K;  // each level consumes >= 8 key bits
+  const int levels = levels_needed ? (int)j.K : 0;  // each level consumes >= 8 key bits
   for (int lv = 0; lv < levels; lv++) {
     if (timed(RS_K_HIST, lv, s, [&] { return launch_hist(j, lv, 0, s); }) < 0) return RS_ERR_CUDA;
     if (timed(RS_K_HIST_REDO, lv, s, [&] { return launch_hist(j, lv, 1, s); }) < 0) return RS_ERR_CUDA;
@@ -309,6 +310,7 @@ static rs_status run_levels(const Setup& st, cudaStream_t s) {
   const u32 gch = (u32)st.sms * (u32)chunk_ctas_per_sm(j);
   if (timed(RS_K_CHUNK, levels, s, [&] { return launch_chunks(j, gch, s); }) < 0) return RS_ERR_CUDA;
   if (timed(RS_K_TINY, levels, s, [&] { return launch_tiny(j, (u32)st.sms, s); }) < 0) return RS_ERR_CUDA;
+  if (levels == 0) return RS_OK;  // (ranges left in tmp come from the levels only)
   if (timed(RS_K_COPY, levels, s, [&] { return launch_copy(j, (u32)st.sms * 2, s); }) < 0) return RS_ERR_CUDA;
   return RS_OK;
 }
@@ -469,7 +471,8 @@ rs_status radix_sort_segmented(void* in, void* tmp, const uint64_t* seg_offsets,
   if ((r = setup_job(in, tmp, total, rec_size, key_size, n_segs, s, &st)) != RS_OK) return r;
   st.j.seg_off = (const u64*)seg_offsets;
   if (timed(RS_K_INIT, 0, s, [&] { return launch_init_segments(st.j, (u32)st.sms * 4, s); }) < 0) return RS_ERR_CUDA;
-  return run_levels(st, s);
+  // no segment can exceed the on-chip limit when all of them together do not: no levels
+  return run_levels(st, s, total > st.j.chunk_max);
 }
 
 static rs_status one_pass(const void* src, void* dst, uint64_t n, uint32_t rec_size, uint32_t key_size,

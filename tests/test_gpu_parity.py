@@ -141,6 +141,26 @@ def test_sort_parity_dominant_key(R, K, pattern):
     np.testing.assert_array_equal(gsort(a, K), oracle.sort(a, K))
 
 
+@pytest.mark.parametrize("R,K", [(16, 8), (24, 16), (8, 3)])
+def test_segmented_small_total(R, K):
+    """All segments together within the on-chip limit: the call launches no distribution level."""
+    rng = np.random.default_rng(R + K)
+    cm = rg.chunk_records(R)
+    sizes = rng.integers(0, 150, 60).astype(np.uint64)
+    while sizes.sum() > cm:
+        sizes = sizes // 2
+    sizes[0] = 70  # one tiny chunk of 33..64 records is not enough: make one on-chip chunk too
+    off = np.concatenate([[0], np.cumsum(sizes)]).astype(np.uint64)
+    n = int(off[-1])
+    assert n <= cm
+    a = rand(rng, n, R, K, distinct=40)
+    t = to_dev(a)
+    rg.sort_segmented(t, torch.from_numpy(off.astype(np.int64)).cuda(), K, total=n)
+    torch.cuda.synchronize()
+    rg.check_status()
+    np.testing.assert_array_equal(from_dev(t), oracle.sort_segmented(a, off, K))
+
+
 def test_segmented_dominant_segments():
     rng = np.random.default_rng(77)
     sizes = np.array([300_000, 50, 120_000, 7, 80_000, 0, 200_000], dtype=np.uint64)

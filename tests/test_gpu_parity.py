@@ -149,7 +149,7 @@ def test_segmented_small_total(R, K):
     sizes = rng.integers(0, 150, 60).astype(np.uint64)
     while sizes.sum() > cm:
         sizes = sizes // 2
-    sizes[0] = 70  # one tiny chunk of 33..64 records is not enough: make one on-chip chunk too
+    sizes[0] = 70  # one segment of more than 64 records: the CTA sorter runs as well as the warps
     off = np.concatenate([[0], np.cumsum(sizes)]).astype(np.uint64)
     n = int(off[-1])
     assert n <= cm

@@ -147,9 +147,9 @@ def test_segmented_small_total(R, K):
     rng = np.random.default_rng(R + K)
     cm = rg.chunk_records(R)
     sizes = rng.integers(0, 150, 60).astype(np.uint64)
-    while sizes.sum() > cm:
-        sizes = sizes // 2
     sizes[0] = 70  # one segment of more than 64 records: the CTA sorter runs as well as the warps
+    while sizes.sum() > cm:
+        sizes[1:] //= 2
     off = np.concatenate([[0], np.cumsum(sizes)]).astype(np.uint64)
     n = int(off[-1])
     assert n <= cm

@@ -254,6 +254,40 @@ __device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commi
 // wait until at most one (the most recent) group of this thread's copies is still pending
 __device__ __forceinline__ void cp_async_wait_one() { asm volatile("cp.async.wait_group 1;\n" ::: "memory"); }
 
+// Bulk copies global -> shared by the copy engine of the SM (one instruction for a whole
+// tile), completed on a shared-memory barrier that counts the bytes that have landed.
+__device__ __forceinline__ unsigned smem_u32(const void* p) { return (unsigned)__cvta_generic_to_shared(p); }
+__device__ __forceinline__ void mbar_init(u64* bar, unsigned count) {
+  asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_u32(bar)), "r"(count) : "memory");
+  asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+}
+// Orders this CTA's earlier ordinary accesses of shared memory (made visible to this thread by
+// a barrier) before the copy engine's writes that follow.
+__device__ __forceinline__ void fence_proxy_async_smem() { asm volatile("fence.proxy.async.shared::cta;" ::: "memory"); }
+// One thread: announce `bytes` on the barrier and start the copy (dst, src, bytes: multiples
+// of 16 bytes and 16-byte aligned).
+__device__ __forceinline__ void bulk_load(void* dst, const void* src, unsigned bytes, u64* bar) {
+  asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_u32(bar)), "r"(bytes) : "memory");
+  asm volatile("cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(
+                   smem_u32(dst)),
+               "l"(src), "r"(bytes), "r"(smem_u32(bar))
+               : "memory");
+}
+// Wait until the barrier's phase `parity` has completed, at most `tries` waits (each one
+// suspends the thread for a bounded time); false if it did not complete.
+__device__ __forceinline__ bool mbar_wait(u64* bar, unsigned parity, unsigned tries) {
+  for (unsigned i = 0; i < tries; i++) {
+    unsigned ok;
+    asm volatile(
+        "{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n selp.u32 %0, 1, 0, p;\n}"
+        : "=r"(ok)
+        : "r"(smem_u32(bar)), "r"(parity)
+        : "memory");
+    if (ok) return true;
+  }
+  return false;
+}
+
 // Exclusive prefix sum over the CTA of one value per thread (NT threads); ends with a barrier.
 template <int NT>
 __device__ __forceinline__ u32 block_exclusive_sum(u32 x, u32* scr) {

@@ -551,8 +551,11 @@ __global__ void __launch_bounds__(kSThreads, 2) k_scatter(Job j, int level) {
   u32* tbase = (u32*)(smem + lay.tbase);
   u64* gbase = (u64*)(smem + lay.gbase);
   __shared__ u32 scan_scr[kSWarps + 1];
+  __shared__ __align__(8) u64 s_bar;  // completes when a tile's bulk copy has landed
   const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
   const u32 ltmask = lanemask_lt();
+  u32 bar_phase = 0;
+  if (tid == 0) mbar_init(&s_bar, 1);
   // per-warp digit counters: counts while ranking, then each warp's offset inside the digit's
   // run; they are zeroed again while the tile is written out
   for (u32 i = tid; i < kSWarps * WSMAX; i += kSThreads) whist[i] = 0;
@@ -599,7 +602,17 @@ __global__ void __launch_bounds__(kSThreads, 2) k_scatter(Job j, int level) {
       const u32 cnt = (u32)min((u64)T, size - r0);
       u64* dstb = j.buf[parity ^ 1];
 
-      load_words_async<kSThreads>(stage, j.buf[parity] + (begin + r0) * RW, (u64)cnt * RW);
+      // the tile comes in by one bulk copy when it starts on a 16-byte boundary (an even word
+      // count per record: always), else by 16- or 8-byte copies of every thread
+      const u64* src = j.buf[parity] + (begin + r0) * RW;
+      const u32 bytes = cnt * RW * 8;
+      const bool bulk = ((((uintptr_t)src) | bytes) & 15) == 0;
+      if (!bulk) {
+        load_words_async<kSThreads>(stage, src, (u64)cnt * RW);
+      } else if (tid == 0) {
+        fence_proxy_async_smem();  // the last tile's reads of the stage are done (barrier)
+        bulk_load(stage, src, bytes, &s_bar);
+      }
       // the lane's next tile of this bin comes into L2 while this one is processed
       if (tid == 0 && t + 1 < t1 && r0 + T < size)
         prefetch_l2(j.buf[parity] + (begin + r0 + T) * RW, min((u64)T, size - r0 - T) * RW * 8);
@@ -613,8 +626,18 @@ __global__ void __launch_bounds__(kSThreads, 2) k_scatter(Job j, int level) {
           run[q] = (q < D && v < nd) ? sg[v] : 0;
         }
       }
-      cp_async_wait_all();
-      __syncthreads();
+      // bounded: a bulk copy that has not landed after 2^20 suspended waits is reported (it
+      // cannot be cancelled, so the CTA waits for it once more before it gives up); every
+      // thread takes the same way out
+      bool failed = false;
+      if (bulk) failed = !mbar_wait(&s_bar, bar_phase, 1u << 20);
+      else cp_async_wait_all();
+      if (__syncthreads_or(failed)) {
+        if (tid == 0) atomicOr(&ctl->err, kErrTimeout);
+        mbar_wait(&s_bar, bar_phase, 1u << 20);
+        return;
+      }
+      if (bulk) bar_phase ^= 1;
 
       // stable rank: warp w owns records [w*PW, (w+1)*PW), visited in order
       u32 packed[IT];

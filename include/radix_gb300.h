@@ -54,7 +54,7 @@ typedef enum rs_status {
   RS_ERR_TOO_LARGE = 4,      /* n * rec_size does not fit in 64 bits / in the address space */
   RS_ERR_NO_MEMORY = 5,      /* the workspace could not be allocated */
   RS_ERR_CUDA = 6,           /* a CUDA runtime call failed (launch, memcpy, sync) */
-  RS_ERR_DEVICE_TIMEOUT = 7, /* reserved (the path has no device-side waits) */
+  RS_ERR_DEVICE_TIMEOUT = 7, /* a bulk copy into shared memory did not land within its bounded wait */
   RS_ERR_QUEUE_OVERFLOW = 8, /* a device-side list overflowed (result undefined) */
   RS_ERR_UNSUPPORTED = 9,    /* a valid request this build does not handle (key_size > 16) */
   RS_ERR_INTERNAL = 10       /* a device-side consistency check failed (result undefined) */

@@ -29,8 +29,12 @@
  * work runs asynchronously on `stream` (NULL = the legacy default stream).  Errors found on
  * the device (a list that overflowed, a destination that failed its range check) set the
  * status word and are reported by radix_sort_status() after the stream has drained; no
- * kernel traps, and no kernel waits for another CTA (the path has no spin-waits).  Calls on one stream run in order; calls on different
- * streams use different workspaces and may overlap.
+ * kernel traps.  No kernel waits for another CTA; the only device-side waits are those of a
+ * CTA for its own bulk copies into shared memory, each bounded (rs_plan.watchdog_polls) and
+ * reported as RS_ERR_DEVICE_TIMEOUT when it runs out.  Once a step of a call has failed, the
+ * call's later kernels do nothing (its result is undefined; `in` is left as the failed step
+ * left it).  Calls on one stream run in order; calls on different streams use different
+ * workspaces and may overlap.
  *
  * Errors.  A call that returns anything but RS_OK launched no work.
  */
@@ -163,7 +167,10 @@ typedef struct rs_plan {
   uint32_t tile_records;    /* records per distribution tile: 256, 512, 1024, 2048 or 4096 */
   uint32_t chunk_records;   /* largest bin sorted on chip: 64.. the shared-memory maximum */
   uint32_t sm_limit;        /* use at most this many SMs for the persistent grids */
-  uint32_t watchdog_polls;  /* reserved, ignored (the path has no device-side waits) */
+  uint32_t watchdog_polls;  /* limit of every device-side wait (a CTA waiting for its own bulk
+                               copy into shared memory): this many suspended polls of the
+                               barrier, then the call reports RS_ERR_DEVICE_TIMEOUT
+                               (default 2^20, about a second) */
 } rs_plan;
 
 rs_status radix_sort_set_plan(const rs_plan *plan);
@@ -231,9 +238,12 @@ int64_t radix_sort_profile_read(rs_kernel_time *out, int64_t max);
  * or fragment it), a latency-critical path where cudaMalloc/cudaFree would add an implicit
  * device synchronisation, or a process with a fixed device-memory budget.  radix_sort
  * allocates its metadata workspace on first use; this entry point instead uses a fixed
- * array of 64 MiB in device memory that the library declares statically (every GPU that
- * loads the library holds it until the process exits).  It calls no cudaMalloc, cudaFree or
- * other allocating routine.
+ * array of 64 MiB in device memory that the library declares statically.  It calls no
+ * cudaMalloc, cudaFree or other allocating routine.  The CUDA runtime reserves the array on
+ * a device when it loads the array's module there: under lazy module loading (the CUDA 12+
+ * default) that happens during the first radix_sort_noalloc call on that device, which can
+ * therefore return RS_ERR_NO_MEMORY when the device is full; from then on the device holds
+ * the array until the process exits, and later calls reserve nothing.
  *
  * Arguments and result are those of radix_sort; the sort is the same (byte-identical
  * output).  Additionally:
@@ -260,10 +270,16 @@ rs_status radix_sort_noalloc(void *in, void *tmp, uint64_t n, uint32_t rec_size,
                              uint32_t *d_status, rs_stream_t stream);
 
 /*
- * Testing only.  flags = 1: in the next call, each distribution pass treats the first
- * non-empty digit run of its first tile as failing the destination range check, so that run
- * is not written: the call completes, its result is undefined, and radix_sort_status()
- * reports RS_ERR_INTERNAL.  The flag applies to one call.  flags = 0 clears it.
+ * Testing only; the flags apply to the next radix_sort / radix_sort_segmented / radix_partition
+ * call on any stream, then clear (flags = 0 clears them at once).
+ *   bit 0 (1): each distribution pass treats the first non-empty digit run of its first tile as
+ *          failing the destination range check, so that run is not written: the call's later
+ *          kernels do nothing, and radix_sort_status() reports RS_ERR_INTERNAL.
+ *   bit 1 (2): the first bulk-copy wait of the first distribution CTA waits on a shared-memory
+ *          barrier that nothing completes, so it runs out after rs_plan.watchdog_polls polls:
+ *          the call's later kernels do nothing, and radix_sort_status() reports
+ *          RS_ERR_DEVICE_TIMEOUT.  (The CTA still waits, with the default limit, for its own
+ *          copy before it exits.)
  */
 rs_status radix_sort_test_inject(uint32_t flags);
 

@@ -41,7 +41,10 @@ static std::atomic<unsigned long long> g_launches{0};
 static std::map<int, int> g_sms;
 static std::atomic<unsigned> g_inject{0};
 
+static std::mutex g_sms_mu;
+
 static int sm_count(int dev) {
+  std::lock_guard<std::mutex> lk(g_sms_mu);
   auto it = g_sms.find(dev);
   if (it != g_sms.end()) return it->second;
   int n = 0;
@@ -217,6 +220,7 @@ static rs_status setup_job(void* in, void* tmp, u64 n, u32 rec_size, u32 key_siz
   j.T = sh.T;
   j.chunk_max = sh.chunk_max;
   j.inject = g_inject.exchange(0);
+  j.wd_polls = p.watchdog_polls ? p.watchdog_polls : kWaitPolls;
   j.n_segs = n_segs;
   int sms = sm_count(dev);
   if (p.sm_limit && (int)p.sm_limit < sms) sms = (int)p.sm_limit;
@@ -316,9 +320,11 @@ static rs_status run_levels(const Setup& st, cudaStream_t s, bool levels_needed 
 }
 
 // ------------------------------------------------------------- no-allocation variant
-// Workspace of radix_sort_noalloc: a fixed array in device memory that every GPU which loads
-// this library holds until the process exits.  Its size bounds the sorts that entry point
-// accepts (see noalloc_setup).
+// Workspace of radix_sort_noalloc: a fixed array in device memory.  CUDA loads the module
+// that holds it on a device when it is first needed there (lazy loading: the first
+// radix_sort_noalloc call on that device, whose address look-up loads it), or with the other
+// modules when lazy loading is off; from then on the device holds the array until the
+// process exits.  Its size bounds the sorts that entry point accepts (see noalloc_setup).
 constexpr size_t kNoAllocBytes = 64ull << 20;
 static __device__ __align__(256) unsigned char g_noalloc_ws[kNoAllocBytes];
 
@@ -337,7 +343,9 @@ static rs_status noalloc_address(int dev, void** out) {
     const cudaError_t e = cudaGetSymbolAddress(&p, g_noalloc_ws);
     if (e != cudaSuccess || !p) {
       cudaGetLastError();
-      return RS_ERR_CUDA;
+      // (under lazy module loading this first look-up is what loads the array's module and
+      // reserves its memory on the device, so it can fail for lack of memory)
+      return e == cudaErrorMemoryAllocation ? RS_ERR_NO_MEMORY : RS_ERR_CUDA;
     }
     g_na_ptr[dev] = p;
   }
@@ -365,6 +373,7 @@ static rs_status noalloc_setup(void* in, void* tmp, u64 n, u32 rec_size, u32 key
   j.wmax = sh.wmax;
   j.T = sh.T;
   j.chunk_max = sh.chunk_max;
+  j.wd_polls = p.watchdog_polls ? p.watchdog_polls : kWaitPolls;
   const Caps c = caps_for(n, j.chunk_max, j.wmax, 0);
   if (c.bytes > kNoAllocBytes) return RS_ERR_TOO_LARGE;
   st->c = c;
@@ -414,6 +423,35 @@ static rs_status noalloc_levels(const Setup& st, cudaStream_t s) {
   return RS_OK;
 }
 
+// radix_sort in two halves: every check and the workspace (sort_prepare), then the launches
+// (sort_launch).  *work = false: nothing to sort (n <= 1).
+static rs_status sort_prepare(void* in, void* tmp, uint64_t n, uint32_t rec_size, uint32_t key_size,
+                              cudaStream_t s, Setup* st, bool* work) {
+  *work = false;
+  rs_status r = validate_layout(rec_size, key_size);
+  if (r != RS_OK) return r;
+  if (n > UINT64_MAX / rec_size) return RS_ERR_TOO_LARGE;
+  if (n <= 1) return RS_OK;
+  if ((r = validate_buffers(in, tmp, n, rec_size)) != RS_OK) return r;
+  if ((r = setup_job(in, tmp, n, rec_size, key_size, 0, s, st)) != RS_OK) return r;
+  *work = true;
+  return RS_OK;
+}
+
+static rs_status sort_launch(const Setup& st, cudaStream_t s) {
+  const Job& j = st.j;
+  const u64 n = j.n;
+  if (n <= j.chunk_max) {
+    if (timed(RS_K_INIT, 0, s, [&] { return launch_init_single_chunk(j, s); }) < 0) return RS_ERR_CUDA;
+    if (timed(RS_K_CHUNK, 0, s, [&] { return launch_chunks(j, 1, s); }) < 0) return RS_ERR_CUDA;
+    return RS_OK;
+  }
+  u32 lo, W;
+  plan_digit(n, 8 * j.K, j.chunk_max, j.wmax, &lo, &W);
+  if (timed(RS_K_INIT, 0, s, [&] { return launch_init_plain(j, lo, W, s); }) < 0) return RS_ERR_CUDA;
+  return run_levels(st, s);
+}
+
 }  // namespace rsg
 
 using namespace rsg;
@@ -421,24 +459,12 @@ using namespace rsg;
 extern "C" {
 
 rs_status radix_sort(void* in, void* tmp, uint64_t n, uint32_t rec_size, uint32_t key_size, rs_stream_t stream) {
-  rs_status r = validate_layout(rec_size, key_size);
-  if (r != RS_OK) return r;
-  if (n > UINT64_MAX / rec_size) return RS_ERR_TOO_LARGE;
-  if (n <= 1) return RS_OK;
-  if ((r = validate_buffers(in, tmp, n, rec_size)) != RS_OK) return r;
   cudaStream_t s = (cudaStream_t)stream;
   Setup st;
-  if ((r = setup_job(in, tmp, n, rec_size, key_size, 0, s, &st)) != RS_OK) return r;
-  const Job& j = st.j;
-  if (n <= j.chunk_max) {
-    if (timed(RS_K_INIT, 0, s, [&] { return launch_init_single_chunk(j, s); }) < 0) return RS_ERR_CUDA;
-    if (timed(RS_K_CHUNK, 0, s, [&] { return launch_chunks(j, 1, s); }) < 0) return RS_ERR_CUDA;
-    return RS_OK;
-  }
-  u32 lo, W;
-  plan_digit(n, 8 * key_size, j.chunk_max, j.wmax, &lo, &W);
-  if (timed(RS_K_INIT, 0, s, [&] { return launch_init_plain(j, lo, W, s); }) < 0) return RS_ERR_CUDA;
-  return run_levels(st, s);
+  bool work = false;
+  const rs_status r = sort_prepare(in, tmp, n, rec_size, key_size, s, &st, &work);
+  if (r != RS_OK || !work) return r;
+  return sort_launch(st, s);
 }
 
 rs_status radix_sort_host(const void* h_in, void* h_out, void* d_buf, void* d_tmp, uint64_t n, uint32_t rec_size,
@@ -449,10 +475,16 @@ rs_status radix_sort_host(const void* h_in, void* h_out, void* d_buf, void* d_tm
   if (n == 0) return RS_OK;
   if (!h_in || !h_out) return RS_ERR_INVALID_ARG;
   if ((r = validate_buffers(d_buf, d_tmp, n, rec_size)) != RS_OK) return r;
-  const size_t bytes = (size_t)(n * rec_size);
+  if (check_device_ptr(d_buf) != RS_OK || check_device_ptr(d_tmp) != RS_OK) return RS_ERR_INVALID_ARG;
   cudaStream_t s = (cudaStream_t)stream;
+  // every check (and the workspace) before the first copy is enqueued: a call that fails
+  // launches nothing
+  Setup st;
+  bool work = false;
+  if ((r = sort_prepare(d_buf, d_tmp, n, rec_size, key_size, s, &st, &work)) != RS_OK) return r;
+  const size_t bytes = (size_t)(n * rec_size);
   if (cudaMemcpyAsync(d_buf, h_in, bytes, cudaMemcpyHostToDevice, s) != cudaSuccess) return RS_ERR_CUDA;
-  if ((r = radix_sort(d_buf, d_tmp, n, rec_size, key_size, stream)) != RS_OK) return r;
+  if (work && (r = sort_launch(st, s)) != RS_OK) return r;
   if (cudaMemcpyAsync(h_out, d_buf, bytes, cudaMemcpyDeviceToHost, s) != cudaSuccess) return RS_ERR_CUDA;
   return RS_OK;
 }
@@ -755,7 +787,7 @@ rs_status radix_sort_noalloc(void* in, void* tmp, uint64_t n, uint32_t rec_size,
 }
 
 rs_status radix_sort_test_inject(uint32_t flags) {
-  if (flags > 1) return RS_ERR_INVALID_ARG;
+  if (flags > (kInjectRange | kInjectWait)) return RS_ERR_INVALID_ARG;
   g_inject = flags;
   return RS_OK;
 }

@@ -25,35 +25,33 @@
 
 namespace rsg {
 
-// Two shapes of the chunk CTA: one CTA of 1,024 threads per SM whose next chunk streams into
-// a second stage buffer while the current one is sorted (kChunkStages = 2), or two CTAs of 512
-// threads per SM with one stage buffer each, which overlap each other (kChunkStages = 1).
-constexpr int kChunkStages = 1;
-constexpr int kCThreads = kChunkStages == 2 ? 1024 : 512;  // threads of a chunk CTA
-constexpr int kChunkCtas = kChunkStages == 2 ? 1 : 2;       // chunk CTAs per SM
+// Two CTAs of 512 threads per SM, each with one stage buffer: one CTA's load and write overlap
+// the other's sort.
+constexpr int kCThreads = 512;   // threads of a chunk CTA
+constexpr int kChunkCtas = 2;    // chunk CTAs per SM
 constexpr int kCWarps = kCThreads / 32;
 constexpr int kEsMax = 48;       // largest bucket finished by enumeration sort
 constexpr int kWinBits = 12;     // digit of the on-chip distribution pass
 constexpr int kIdxBits = 13;     // input positions of a chunk (chunk_max <= 2^13)
-constexpr int kChunkItems = kChunkStages == 2 ? 8 : 10;  // positions per thread (chunk_max <= kCThreads * this)
+constexpr int kChunkItems = 9;   // positions per thread (chunk_max <= kCThreads * this)
 constexpr int kCntWords = 1 << (kWinBits - 1);  // counters of a distribution, two 16-bit per word
-// shared memory of the chunk CTA, and the part that is not per record
-constexpr size_t kChunkSmem = kChunkStages == 2 ? 220 * 1024 : 108 * 1024;
-constexpr size_t kChunkFixed = kCntWords * 4 + 4 * 1024;
+// dynamic shared memory of the chunk CTA (two CTAs and their static shared memory fit an SM)
+constexpr size_t kChunkSmem = 111 * 1024;
+constexpr size_t kChunkFixed = kCntWords * 4 + 256;
 
+// stage: the chunk's records; aux: one composite key (u64) per record in the first round, or
+// the two index arrays (u16) and the bucket stack of the general rounds; cnt: the counters.
 struct ChunkLayout {
-  size_t stage, perm, out, cnt, stack, total;
+  size_t stage, aux, cnt, total;
 };
 
 __host__ __device__ inline ChunkLayout chunk_layout(u32 m, u32 RW) {
   ChunkLayout c;
   size_t o = 0;
-  c.stage = o; o += kChunkStages * (size_t)m * RW * 8;  // stage buffer(s) of the records
-  c.perm = o; o += (size_t)m * 2;
-  c.out = o; o += (size_t)m * 2;
+  c.stage = o; o += (size_t)m * RW * 8;
+  c.aux = o; o += (size_t)m * 8;  // >= 4m (perm, out) + the stack of at most m / (kEsMax + 1) + 2 pairs
   o = (o + 15) & ~(size_t)15;
   c.cnt = o; o += (size_t)kCntWords * 4;
-  c.stack = o; o += (size_t)(m / (kEsMax + 1) + 2) * 8;
   c.total = (o + 127) & ~(size_t)127;
   return c;
 }
@@ -80,8 +78,9 @@ struct ChunkCtx {
 };
 
 // Exclusive scan, in place, of nd (even, <= 2^kWinBits) 16-bit counters packed two per word.
+// Returns (the same in every thread) whether some counter exceeded `big`.
 template <int KW, int RWT>
-__device__ void scan_counts(const ChunkCtx<KW, RWT>& c, u32 nd) {
+__device__ bool scan_counts(const ChunkCtx<KW, RWT>& c, u32 nd, u32 big = 0xffffu) {
   __shared__ u32 scr[kCWarps + 1];
   const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
   const u32 words = nd >> 1;
@@ -89,18 +88,21 @@ __device__ void scan_counts(const ChunkCtx<KW, RWT>& c, u32 nd) {
   const u32 w0 = min(words, tid * per), w1 = min(words, w0 + per);
   // four words per thread (a full window's counters): one 16-byte access instead of four
   // accesses of consecutive words per lane, which meet a 4-way bank conflict
-  u32 sum = 0;
+  u32 sum = 0, mx = 0;
   uint4 v4 = make_uint4(0, 0, 0, 0);
   const bool vec = per == 4 && w1 - w0 == 4;
+  auto take = [&](u32 x) {
+    sum += (x & 0xffffu) + (x >> 16);
+    mx = max(mx, max(x & 0xffffu, x >> 16));
+  };
   if (vec) {
     v4 = *reinterpret_cast<const uint4*>(c.cnt + w0);
-    sum = (v4.x & 0xffffu) + (v4.x >> 16) + (v4.y & 0xffffu) + (v4.y >> 16) + (v4.z & 0xffffu) + (v4.z >> 16) +
-          (v4.w & 0xffffu) + (v4.w >> 16);
+    take(v4.x);
+    take(v4.y);
+    take(v4.z);
+    take(v4.w);
   } else {
-    for (u32 w = w0; w < w1; w++) {
-      const u32 x = c.cnt[w];
-      sum += (x & 0xffffu) + (x >> 16);
-    }
+    for (u32 w = w0; w < w1; w++) take(c.cnt[w]);
   }
   u32 x = sum;
 #pragma unroll
@@ -143,7 +145,7 @@ __device__ void scan_counts(const ChunkCtx<KW, RWT>& c, u32 nd) {
       run = hi + (v >> 16);
     }
   }
-  __syncthreads();
+  return __syncthreads_or(mx > big) != 0;
 }
 
 // The digit of an on-chip distribution: key bits [lo, lo + w), optionally preceded (as more
@@ -176,6 +178,57 @@ __device__ __forceinline__ DigitSpec window_below(u32 p, u32 s = 1u << kIdxBits)
   d.w = p > w ? w : p;
   d.lo = p - d.w;
   return d;
+}
+
+// The first on-chip round of a chunk sorts 64-bit composite keys: the record's relevant key
+// bits -- a packed chunk's sub-bin number (sb bits) above key bits [0, p), every higher key bit
+// being shared by the chunk -- cut from below to their top kCompKeyBits bits, then the record's
+// position in the chunk (kIdxBits).  Composite keys are distinct (positions are), so ranking a
+// bucket needs one comparison of neighbouring words per pair; their order is the (key,
+// position) order, except between two records whose kept key bits are equal while dropped
+// ones (t > 0) differ: those compare their whole keys.
+constexpr u32 kCompKeyBits = 64 - kIdxBits;
+
+struct CompSpec {
+  u64 m0, m1;         // key bits [0, p) of words 0 and 1
+  u32 p, sb, plo, pw, v0;
+  u32 t;              // relevant key bits dropped from below (0: the composite order is exact)
+  u32 dshift, dmask;  // the round's digit = (composite >> dshift) & dmask (= DigitSpec::of)
+
+  // relevant key bits [t, p + sb) of a key, at bit 0
+  template <int KW>
+  __device__ __forceinline__ u64 keypart(const Key<KW>& k) const {
+    u64 lo = k.w[0] & m0, hi = KW == 2 ? (k.w[KW - 1] & m1) : 0ull;
+    if (sb) {
+      const u64 sub = (u64)((digit_of<KW>(k, plo, pw) - v0) & ((1u << sb) - 1u));
+      if (p < 64) {
+        lo |= sub << p;
+        if (p + sb > 64) hi |= sub >> (64 - p);
+      } else {
+        hi |= sub << (p - 64);
+      }
+    }
+    if (t == 0) return lo;
+    if (t < 64) return (lo >> t) | (hi << (64 - t));
+    return hi >> (t - 64);
+  }
+};
+
+// Composite keys for a round whose digit `dig` sits right below bit p (dig.lo + dig.w = p).
+__device__ __forceinline__ CompSpec comp_spec(const DigitSpec& dig, u32 p, u64 km0, u64 km1) {
+  CompSpec cs;
+  cs.p = p;
+  cs.sb = dig.sb;
+  cs.plo = dig.plo;
+  cs.pw = dig.pw;
+  cs.v0 = dig.v0;
+  cs.m0 = (p >= 64 ? ~0ull : ((1ull << p) - 1ull)) & km0;
+  cs.m1 = (p <= 64 ? 0ull : p >= 128 ? ~0ull : ((1ull << (p - 64)) - 1ull)) & km1;
+  const u32 kb = p + dig.sb;
+  cs.t = kb > kCompKeyBits ? kb - kCompKeyBits : 0u;
+  cs.dshift = kIdxBits + dig.lo - cs.t;  // (the digit lies inside the kept bits)
+  cs.dmask = (1u << dig.bits()) - 1u;
+  return cs;
 }
 
 // Distributes positions [a, a + s) of c.perm into c.out by a digit of the record (any order
@@ -216,15 +269,14 @@ __device__ void distribute(const ChunkCtx<KW, RWT>& c, u32 a, u32 s, const Digit
   __syncthreads();
 }
 
-// Sorts positions [a, a + s) of c.perm by (key, input position): one distribution by `dig`,
-// then enumeration sort of every bucket of up to kEsMax records; larger buckets go on the
-// stack.  Ends with a barrier, after which *s_top is final.
+// After a distribution of positions [a, a + s) by `dig` into c.out (bucket starts in c.cnt):
+// enumeration sort of every bucket of up to kEsMax records into c.perm; the positions of a
+// larger bucket are copied as they are and the bucket goes on the stack.  Ends with a
+// barrier, after which *s_top is final.
 template <int KW, int RWT>
-__device__ void sort_round(const ChunkCtx<KW, RWT>& c, u32 a, u32 s, const DigitSpec& dig, u32* s_top,
-                           bool identity = false, bool zeroed = false) {
+__device__ void finish_round(const ChunkCtx<KW, RWT>& c, u32 a, u32 s, const DigitSpec& dig, u32* s_top) {
   const int tid = threadIdx.x;
   const u32 nd = 1u << dig.bits();
-  distribute(c, a, s, dig, identity, zeroed);
   for (u32 i = tid; i < s; i += kCThreads) {
     const u32 r = c.out[a + i];
     const Key<KW> kr = c.key(r);
@@ -255,6 +307,14 @@ __device__ void sort_round(const ChunkCtx<KW, RWT>& c, u32 a, u32 s, const Digit
     }
   }
   __syncthreads();
+}
+
+// Sorts positions [a, a + s) of c.perm by (key, input position): one distribution by `dig`,
+// then finish_round.
+template <int KW, int RWT>
+__device__ void sort_round(const ChunkCtx<KW, RWT>& c, u32 a, u32 s, const DigitSpec& dig, u32* s_top) {
+  distribute(c, a, s, dig, false, false);
+  finish_round(c, a, s, dig, s_top);
 }
 
 // Highest differing key bit + 1 over positions [a, a + s) (through c.perm, or the identity)
@@ -351,15 +411,25 @@ __device__ __noinline__ void small_chunk_sort(const ChunkCtx<KW, RWT>& c, u32 sz
   __syncthreads();
 }
 
-// Persistent CTAs take chunks by ticket.  With two stage buffers the next chunk's records
-// stream in while the current chunk is sorted; with one, the CTAs sharing an SM overlap.
+// Persistent CTAs take chunks by ticket; the two CTAs of an SM overlap each other's load,
+// sort and write.  Per chunk: one bulk copy of its records into shared memory (bounded wait;
+// the next chunk's records are meanwhile prefetched into L2), then
+//   * more than kEsMax records: the first distribution counts the digit right below the
+//     chunk's shared bits and keeps every record's composite key (CompSpec).  If no bucket
+//     holds more than kEsMax records, the composite keys go to their buckets and a record's
+//     place is its bucket's start plus the number of smaller composite keys in the bucket;
+//     records of 8 or 16 bytes are written straight there, larger ones through the order
+//     array.  Otherwise the round goes on with record indices (finish_round) and recurses on
+//     the buckets it leaves on the stack;
+//   * at most kEsMax records: one enumeration sort of the whole chunk;
+//   * already in order: copied to `in` if it lives in tmp.
 template <int KW, int RWT>
 __global__ void __launch_bounds__(kCThreads, kChunkCtas) k_chunk(Job j) {
   Ctl* ctl = j.ctl;
   const u64 nch = ctl->nchunks;
-  if (nch == 0) return;
+  if (nch == 0 || call_failed(ctl)) return;
   if (nch + ctl->ntiny > j.cap_chunks) {  // the two lists met (reported when they were filled)
-    if (blockIdx.x == 0 && threadIdx.x == 0) atomicOr(&ctl->err, kErrOverflow);
+    if (blockIdx.x == 0 && threadIdx.x == 0) report(ctl, kErrOverflow);
     return;
   }
   const u32 RW = RWT ? (u32)RWT : j.RW;
@@ -370,38 +440,37 @@ __global__ void __launch_bounds__(kCThreads, kChunkCtas) k_chunk(Job j) {
   c.km0 = j.keymask[0];
   c.km1 = j.keymask[1];
   c.RW = RW;
-  u64* stage0 = (u64*)(smem + lay.stage);
-  c.perm = (u16*)(smem + lay.perm);
-  c.out = (u16*)(smem + lay.out);
-  c.cnt = (u32*)(smem + lay.cnt);
-  c.stack = (u32*)(smem + lay.stack);
+  u64* stage = (u64*)(smem + lay.stage);
+  c.stage = stage;
+  u64* comp = (u64*)(smem + lay.aux);  // first round: composite keys
+  c.perm = (u16*)(smem + lay.aux);     // general rounds: two order arrays and the stack
+  c.out = c.perm + m;
+  c.stack = (u32*)(smem + lay.aux + (size_t)m * 4);
   c.stack_cap = m / (kEsMax + 1) + 2;
-  __shared__ Chunk s_ch[2];
-  __shared__ u64 s_t[2];
+  c.cnt = (u32*)(smem + lay.cnt);
+  __shared__ Chunk s_ch;
+  __shared__ u64 s_t;
   __shared__ u32 s_top;
+  __shared__ __align__(8) u64 s_bar;  // completes when a chunk's bulk copy has landed
   const int tid = threadIdx.x;
+  constexpr u32 kIdxMask = (1u << kIdxBits) - 1u;
+  u32 bar_phase = 0;
 
-  // thread 0: take a ticket and read its chunk (an unusable descriptor is reported, not used)
-  auto fetch = [&](int slot, u64 t) {
+  // thread 0: publish ticket t with its descriptor `raw` (an unusable one is reported, not
+  // used) and ask for its records to be brought into L2
+  auto fetch = [&](u64 t, Chunk raw) {
     Chunk ch = {};
     if (t < nch) {
-      ch = j.chunks[t];
+      ch = raw;
       if (ch.size > m || ch.begin > j.n || ch.begin + ch.size > j.n) {
-        atomicOr(&ctl->err, kErrInternal);
+        report(ctl, kErrInternal);
         ch.size = 0;
       }
+      if (ch.size) prefetch_l2(j.buf[(ch.flags & kChSrcTmp) ? 1 : 0] + ch.begin * RW, (u64)ch.size * RW * 8);
     }
-    s_ch[slot] = ch;
-    s_t[slot] = t;
+    s_ch = ch;
+    s_t = t;
   };
-  auto issue = [&](int slot) {
-    const Chunk& ch = s_ch[slot];
-    if (s_t[slot] < nch && ch.size)
-      load_words_async<kCThreads>(stage0 + (size_t)slot * m * RW,
-                                  j.buf[(ch.flags & kChSrcTmp) ? 1 : 0] + ch.begin * RW, (u64)ch.size * RW);
-    cp_async_commit();
-  };
-
   // Tickets are dispensed in batches when chunks are many (many tiny segments): thread 0
   // owns tickets [t_next, t_end) and takes the next batch with one atomic.
   const u64 batch = nch >= (u64)gridDim.x * 2048 ? 8 : 1;
@@ -415,83 +484,175 @@ __global__ void __launch_bounds__(kCThreads, kChunkCtas) k_chunk(Job j) {
   };
   for (u32 i = tid; i < (u32)kCntWords; i += kCThreads) c.cnt[i] = 0;
   if (tid == 0) {
-    fetch(0, take());
-    if (kChunkStages == 2) fetch(1, take());
+    mbar_init(&s_bar, 1);
+    const u64 t = take();
+    Chunk raw = {};
+    if (t < nch) raw = j.chunks[t];
+    fetch(t, raw);
   }
   __syncthreads();
-  if (kChunkStages == 2) {
-    issue(0);
-    issue(1);
-  }
-  int cur = 0;
   for (;;) {
-    if (kChunkStages == 2) {
-      cp_async_wait_one();
-      __syncthreads();
-    }
-    if (s_t[cur] >= nch) break;  // a CTA's tickets only grow: no later chunk either
-    const Chunk ch = s_ch[cur];
-    if (kChunkStages == 1) issue(cur);
-    u64 nt = 0;
-    if (tid == 0) nt = take();  // described during this chunk
-    if (kChunkStages == 1) {
-      cp_async_wait_all();
-      __syncthreads();
-    }
+    if (s_t >= nch) break;  // a CTA's tickets only grow: no later chunk either
+    const Chunk ch = s_ch;
     const u32 sz = ch.size;
-    c.stage = stage0 + (size_t)cur * m * RW;
-    const u64* stage = c.stage;
+    const bool in_place = !(ch.flags & kChSrcTmp), copy_only = (ch.flags & kChCopyOnly) != 0;
+    // the records come in by one bulk copy when they start on a 16-byte boundary (an even
+    // word count per record: always), else by 16- or 8-byte copies of every thread
+    const u64* src = j.buf[in_place ? 0 : 1] + ch.begin * RW;
+    const u32 bytes = sz * RW * 8;
+    const bool load = sz && !(copy_only && in_place);
+    const bool bulk = load && ((((uintptr_t)src) | bytes) & 15) == 0;
+    if (load && !bulk) load_words_async<kCThreads>(stage, src, (u64)sz * RW);
+    if (bulk && tid == 0) {
+      fence_proxy_async_smem();  // the last chunk's reads of the stage are done (barrier)
+      bulk_load(stage, src, bytes, &s_bar);
+    }
+    u64 nt = 0;
+    Chunk nraw = {};
+    if (tid == 0) {  // the next ticket and its descriptor (published after the wait)
+      nt = take();
+      if (nt < nch) nraw = j.chunks[nt];
+    }
+    // bounded wait (the copy cannot be cancelled: after a timeout the CTA still waits for it,
+    // with the default limit, before it leaves)
+    bool failed = false;
+    if (bulk) failed = !mbar_wait(&s_bar, bar_phase, j.wd_polls);
+    else cp_async_wait_all();
+    if (__syncthreads_or(failed)) {
+      if (tid == 0) report(ctl, kErrTimeout);
+      mbar_wait(&s_bar, bar_phase, kWaitPolls);
+      return;
+    }
+    if (bulk) bar_phase ^= 1;
+    if (tid == 0) fetch(nt, nraw);  // every thread has read s_ch and s_t (barrier above)
+
     u64* dst = j.buf[0] + ch.begin * RW;
-    const bool in_place = !(ch.flags & kChSrcTmp);
     DigitSpec dig = {};
-    bool sort = sz && !(ch.flags & kChCopyOnly);
+    u32 p = ch.p;
+    bool sort = sz && !copy_only;
     if (sort) {
-      if (ch.p) {  // shared bits known from the level that produced the chunk
-        dig = window_below(ch.p, sz);
+      if (p) {  // shared bits known from the level that produced the chunk
+        dig = window_below(p, sz);
         if (ch.sb) {
           dig.sb = ch.sb;
-          dig.plo = ch.p;
+          dig.plo = p;
           dig.pw = ch.pw;
           dig.v0 = ch.v0;
-          dig.w = ch.p > (u32)kWinBits - ch.sb ? (u32)kWinBits - ch.sb : ch.p;
-          dig.lo = ch.p - dig.w;
+          dig.w = p > (u32)kWinBits - ch.sb ? (u32)kWinBits - ch.sb : p;
+          dig.lo = p - dig.w;
         }
       } else {
-        const u32 p = range_top_bit(c, 0, sz, false);  // (ends with a barrier)
+        p = range_top_bit(c, 0, sz, false);  // (ends with a barrier)
         sort = p != 0;
         dig = window_below(p, sz);
       }
     }
+    bool via_perm = false;  // the sorted order is in c.perm (else the records are written)
     if (sort && sz > (u32)kEsMax) {
+      // first round: count the digit, keeping every record's composite key
+      const CompSpec cs = comp_spec(dig, p, c.km0, c.km1);
+      u64 ck[kChunkItems];
+      u32 held[kChunkItems];  // (digit << 16) | rank among the digit's records counted before
+#pragma unroll
+      for (int k = 0; k < kChunkItems; k++) {
+        const u32 i = tid + k * kCThreads;
+        held[k] = 0xffffffffu;
+        ck[k] = 0;
+        if (i < sz) {
+          ck[k] = (cs.keypart<KW>(c.key(i)) << kIdxBits) | i;
+          const u32 d = (u32)(ck[k] >> cs.dshift) & cs.dmask;
+          const u32 old = atomicAdd(&c.cnt[d >> 1], 1u << ((d & 1) * 16));
+          held[k] = ((old >> ((d & 1) * 16)) & 0xffffu) | (d << 16);
+        }
+      }
       if (tid == 0) s_top = 0;
-      // s_ch[cur] has been read by every thread (a barrier lies inside sort_round before
-      // thread 0 rewrites it below)
-      sort_round(c, 0, sz, dig, &s_top, true, true);
-      if (tid == 0) fetch(cur, nt);
-      while (s_top) {  // s_top is final after the barrier that ends every round
-        const u32 top = s_top;
-        if (top > c.stack_cap) {  // cannot happen: buckets on the stack are disjoint and > kEsMax
-          if (tid == 0) atomicOr(&ctl->err, kErrInternal);
-          break;
-        }
-        const u32 a = c.stack[2 * (top - 1)], s = c.stack[2 * (top - 1) + 1];
+      __syncthreads();
+      const u32 nd = cs.dmask + 1;
+      const bool big = scan_counts(c, nd < 2 ? 2 : nd, (u32)kEsMax);  // (ends with a barrier)
+      if (!big) {
+#pragma unroll
+        for (int k = 0; k < kChunkItems; k++)
+          if (held[k] != 0xffffffffu) comp[c.count_of(held[k] >> 16) + (held[k] & 0xffffu)] = ck[k];
         __syncthreads();
-        if (tid == 0) s_top = top - 1;
-        __syncthreads();
-        const u32 pp = range_top_bit(c, a, s, true);
-        if (pp) {
-          sort_round(c, a, s, window_below(pp), &s_top);
-        } else {  // all keys equal: back to input order
-          restore_input_order(c, a, s);
+        // a record's place: its bucket's start + the smaller composite keys of its bucket
+        u32 placed[kChunkItems];  // (place << 16) | record, for records of more than 16 bytes
+#pragma unroll
+        for (int k = 0; k < kChunkItems; k++) {
+          const u32 i = tid + k * kCThreads;
+          placed[k] = 0xffffffffu;
+          if (i < sz) {
+            const u64 cm = comp[i];
+            const u32 d = (u32)(cm >> cs.dshift) & cs.dmask;
+            const u32 st = c.count_of(d), en = d < cs.dmask ? c.count_of(d + 1) : sz;
+            u32 rank = 0;
+            if (cs.t == 0) {
+              for (u32 q = st; q < en; q++) rank += comp[q] < cm;
+            } else {
+              for (u32 q = st; q < en; q++) {
+                const u64 cq = comp[q];
+                bool lt = cq < cm;
+                if (cq != cm && (cq ^ cm) <= (u64)kIdxMask) {  // equal kept key bits: whole keys
+                  const Key<KW> kq = c.key((u32)cq & kIdxMask), km = c.key((u32)cm & kIdxMask);
+                  lt = key_less<KW>(kq, km) || (key_eq<KW>(kq, km) && cq < cm);
+                }
+                rank += lt;
+              }
+            }
+            const u32 r = (u32)cm & kIdxMask, pos = st + rank;
+            if (RW <= 2) {
+              const u64* sp = stage + (u64)r * RW;
+              u64* dp = dst + (u64)pos * RW;
+              if (RW == 2)
+                __stcs(reinterpret_cast<ulonglong2*>(dp), *reinterpret_cast<const ulonglong2*>(sp));
+              else
+                __stcs(dp, sp[0]);
+            } else {
+              placed[k] = (pos << 16) | r;
+            }
+          }
         }
+        __syncthreads();  // composite keys and counters are read
+        if (RW > 2) {
+#pragma unroll
+          for (int k = 0; k < kChunkItems; k++)
+            if (placed[k] != 0xffffffffu) c.perm[placed[k] >> 16] = (u16)(placed[k] & 0xffffu);
+          via_perm = true;
+        }
+      } else {
+        // a bucket of more than kEsMax records: the general rounds, on record indices
+#pragma unroll
+        for (int k = 0; k < kChunkItems; k++)
+          if (held[k] != 0xffffffffu)
+            c.out[c.count_of(held[k] >> 16) + (held[k] & 0xffffu)] = (u16)(tid + k * kCThreads);
+        __syncthreads();
+        finish_round(c, 0, sz, dig, &s_top);
+        while (s_top) {  // s_top is final after the barrier that ends every round
+          const u32 top = s_top;
+          if (top > c.stack_cap) {  // cannot happen: buckets on the stack are disjoint and > kEsMax
+            if (tid == 0) report(ctl, kErrInternal);
+            break;
+          }
+          const u32 a = c.stack[2 * (top - 1)], s = c.stack[2 * (top - 1) + 1];
+          __syncthreads();
+          if (tid == 0) s_top = top - 1;
+          __syncthreads();
+          const u32 pp = range_top_bit(c, a, s, true);
+          if (pp) {
+            sort_round(c, a, s, window_below(pp), &s_top);
+          } else {  // all keys equal: back to input order
+            restore_input_order(c, a, s);
+          }
+        }
+        via_perm = true;
       }
       // counters back to zero for the next chunk's first distribution
       for (u32 i = tid; i < (u32)kCntWords; i += kCThreads) c.cnt[i] = 0;
+      __syncthreads();  // (the order array is complete)
     } else if (sort) {
-      small_chunk_sort(c, sz);  // (ends with a barrier: every thread has read s_ch[cur])
-      if (tid == 0) fetch(cur, nt);
+      small_chunk_sort(c, sz);  // (ends with a barrier)
+      via_perm = true;
     }
-    if (sort) {
+    if (via_perm) {
       // write the records in sorted order
       if (RW == 2) {
         for (u32 s = tid; s < sz; s += kCThreads) {
@@ -522,27 +683,19 @@ __global__ void __launch_bounds__(kCThreads, kChunkCtas) k_chunk(Job j) {
             __stcs(d + piece, sp[piece]);
         }
       }
-    } else {
-      if (sz && !in_place) {  // already in order, but in tmp
-        const u64 words = (u64)sz * RW;
-        for (u64 i = tid; i < words; i += kCThreads) __stcs(dst + i, stage[i]);
-      }
-      __syncthreads();  // every thread has read s_ch[cur]
-      if (tid == 0) fetch(cur, nt);
+    } else if (!sort && sz && !in_place) {  // already in order, but in tmp
+      const u64 words = (u64)sz * RW;
+      for (u64 i = tid; i < words; i += kCThreads) __stcs(dst + i, stage[i]);
     }
-    __syncthreads();  // stage buffer `cur` is free and s_ch[cur] describes the next chunk
-    if (kChunkStages == 2) {
-      issue(cur);
-      cur ^= 1;
-    }
+    __syncthreads();  // the stage is free and s_ch describes the next chunk
   }
-  cp_async_wait_all();
 }
 
 // Finished ranges that live in tmp: copy to in.
 __global__ void __launch_bounds__(kThreads) k_copy(Job j) {
   Ctl* ctl = j.ctl;
   const u64 np = ctl->npieces;
+  if (np == 0 || call_failed(ctl)) return;
   __shared__ u64 s_ticket;
   for (;;) {
     if (threadIdx.x == 0) s_ticket = atomicAdd(&ctl->piece_ticket, 1ull);
@@ -552,7 +705,7 @@ __global__ void __launch_bounds__(kThreads) k_copy(Job j) {
     if (t >= np) break;
     const Piece pc = j.pieces[t];
     if (pc.begin > j.n || pc.size > j.n - pc.begin) {
-      if (threadIdx.x == 0) atomicOr(&ctl->err, kErrInternal);
+      if (threadIdx.x == 0) report(ctl, kErrInternal);
       continue;
     }
     const u64 words = pc.size * j.RW;
@@ -714,9 +867,9 @@ template <int KW>
 __global__ void __launch_bounds__(kTinyThreads) k_tiny(Job j) {
   Ctl* ctl = j.ctl;
   const u64 nt = ctl->ntiny;
-  if (nt == 0) return;
+  if (nt == 0 || call_failed(ctl)) return;
   if (ctl->nchunks + nt > j.cap_chunks) {  // the two lists met (reported when they were filled)
-    if (blockIdx.x == 0 && threadIdx.x == 0) atomicOr(&ctl->err, kErrOverflow);
+    if (blockIdx.x == 0 && threadIdx.x == 0) report(ctl, kErrOverflow);
     return;
   }
   extern __shared__ __align__(16) unsigned char smem[];
@@ -733,7 +886,7 @@ __global__ void __launch_bounds__(kTinyThreads) k_tiny(Job j) {
     if (lane < nb) {
       const Chunk ch = j.chunks[j.cap_chunks - 1 - (t0 + lane)];
       if (ch.size > kTinyMax || ch.begin > j.n || ch.begin + ch.size > j.n) {
-        atomicOr(&ctl->err, kErrInternal);
+        report(ctl, kErrInternal);
       } else {
         c_begin = ch.begin;
         c_size = ch.size;
@@ -836,11 +989,11 @@ int launch_copy(const Job& j, u32 grid, cudaStream_t s) {
   return cudaGetLastError() == cudaSuccess ? 1 : -1;
 }
 
-// chunk_max for a record size: the largest range whose two staging buffers and index arrays
-// fit the shared memory of the chunk CTA (and whose positions fit kIdxBits bits).
+// chunk_max for a record size: the largest range whose staged records and composite keys fit
+// the shared memory of the chunk CTA (and whose positions fit kIdxBits bits).
 u32 chunk_capacity(u32 RW) {
   const size_t budget = kChunkSmem - kChunkFixed;
-  u32 m = (u32)(budget / (kChunkStages * RW * 8 + 4));  // staged copies of the record + two u16 index arrays
+  u32 m = (u32)(budget / (RW * 8 + 8));  // the staged record + its composite key (or two u16 indices)
   m &= ~63u;
   if (m > (u32)kCThreads * kChunkItems) m = kCThreads * kChunkItems;
   if (m > (1u << kIdxBits)) m = 1u << kIdxBits;

@@ -31,6 +31,13 @@ constexpr u32 kFull = 0xffffffffu;
 // device error bits (reported by radix_sort_status)
 enum : u32 { kErrTimeout = 1u, kErrOverflow = 2u, kErrInternal = 4u };
 
+// testing hooks (radix_sort_test_inject): one digit run of the first scatter tile fails its
+// range check; the first scatter tile waits on a barrier that nothing completes
+enum : u32 { kInjectRange = 1u, kInjectWait = 2u };
+
+// default limit of a device-side wait: 2^20 suspended polls (about a second)
+constexpr u32 kWaitPolls = 1u << 20;
+
 // Bin flags
 enum : u32 { kBinRedo = 1u, kBinEqual = 2u, kBinDom = 4u };
 
@@ -79,8 +86,12 @@ struct Piece {
 };
 
 // Control block in device memory.  Lists are double-buffered by level parity.
+// `err` collects the error bits of every call on the stream until radix_sort_status reads
+// it; `cerr` holds those of the current call only (the call's first kernel clears it), and
+// every kernel after the one that set it returns at once: nothing computed from records that
+// a failed step left unwritten reaches a later kernel.
 struct Ctl {
-  u32 err, pad0;
+  u32 err, cerr;
   u64 nbins[2];
   u64 ntiles[2];
   u64 base_used[2];
@@ -102,7 +113,8 @@ struct Job {
   u32 chunk_max;      // largest range one CTA sorts on chip
   u32 wmax;           // widest digit of a pass (<= kWMax)
   u32 lanes;          // tile ranges of a distribution level (one per histogram CTA)
-  u32 inject;         // testing: 1 = the first scatter pass finds one digit run out of range
+  u32 inject;         // testing: kInjectRange / kInjectWait (one call)
+  u32 wd_polls;       // limit of a device-side wait (suspended polls of a shared-memory barrier)
 
   u64 keymask[2];     // key bits of words 0 and 1
   Ctl* ctl;
@@ -119,6 +131,14 @@ struct Job {
   const u64* seg_off; // segmented mode: n_segs + 1 record offsets
   u64 n_segs;
 };
+
+// Records an error of the current call (and in the stream's sticky word).
+__device__ __forceinline__ void report(Ctl* ctl, u32 bits) {
+  atomicOr(&ctl->err, bits);
+  atomicOr(&ctl->cerr, bits);
+}
+// Whether an earlier step of the current call failed (then a kernel does nothing).
+__device__ __forceinline__ bool call_failed(const Ctl* ctl) { return *(volatile const u32*)&ctl->cerr != 0; }
 
 constexpr u64 kPieceRecords = 1ull << 16;      // copy-back granularity
 constexpr u32 kMaxLanes = 1024;                // tile ranges per level, at most

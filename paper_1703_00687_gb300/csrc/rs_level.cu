@@ -146,7 +146,7 @@ __global__ void __launch_bounds__(kThreads) k_init_segments(Job j) {
       const u64 e = j.seg_off[s + 1];
       a = j.seg_off[s];
       if (e < a || e > j.n) {  // offsets not non-decreasing within [0, total]: skip, report
-        atomicOr(&ctl->err, kErrInternal);
+        report(ctl, kErrInternal);
       } else if (e > a + 1) {
         c = e - a;
         to_tiny = c <= kTinyMax;
@@ -170,7 +170,7 @@ __global__ void __launch_bounds__(kThreads) k_init_segments(Job j) {
     if (to_chunk || to_tiny) {
       const u64 t = to_tiny ? first_t + __popc(want_t & lanemask_lt()) : first + __popc(want & lanemask_lt());
       if (t >= j.cap_chunks) {
-        atomicOr(&ctl->err, kErrOverflow);
+        report(ctl, kErrOverflow);
       } else {
         Chunk ch = {};
         ch.begin = a;
@@ -185,7 +185,7 @@ __global__ void __launch_bounds__(kThreads) k_init_segments(Job j) {
     const u64 idx = atomicAdd(&ctl->nbins[0], 1ull);
     const u64 bo = atomicAdd(&ctl->base_used[0], (u64)nd);
     if (idx >= j.cap_bins || bo + nd > j.cap_base) {
-      atomicOr(&ctl->err, kErrOverflow);
+      report(ctl, kErrOverflow);
       continue;
     }
     Bin bn = {};
@@ -270,7 +270,7 @@ __device__ void finish_bin(const Job& j, int L, u64 b, int mode) {
   const u64 ts = bp->tile_start, nt = ceil_div(size, (u64)j.T);
   const u64 cfirst = ts / per, clast = (ts + nt - 1) / per;
   if (clast + b >= j.cap_seg) {  // cannot happen: lanes + bins segments are allocated
-    if (threadIdx.x == 0) atomicOr(&j.ctl->err, kErrOverflow);
+    if (threadIdx.x == 0) report(j.ctl, kErrOverflow);
     return;
   }
   u64 r0 = ex, r1 = ex + c0;
@@ -299,7 +299,7 @@ __global__ void __launch_bounds__(kThreads, 2) k_hist(Job j, int level, int mode
   const int L = level & 1;
   Ctl* ctl = j.ctl;
   const u64 nb = ctl->nbins[L];
-  if (nb == 0) return;
+  if (nb == 0 || call_failed(ctl)) return;
   if (mode == 1 && ctl->nredo == 0) return;
   const u64 ntiles = ctl->ntiles[L];
   Bin* bins = j.bins[L];
@@ -329,7 +329,7 @@ __global__ void __launch_bounds__(kThreads, 2) k_hist(Job j, int level, int mode
     const u64 bo = bb->base_off;
     const u64 sid = lane_id + b;  // segment of (lane, bin)
     if (sid >= j.cap_seg) {    // cannot happen: lanes + bins segments are allocated
-      if (tid == 0) atomicOr(&ctl->err, kErrOverflow);
+      if (tid == 0) report(ctl, kErrOverflow);
       return;
     }
     u64* sg = j.seg + (sid << j.wmax);
@@ -535,7 +535,7 @@ __global__ void __launch_bounds__(kSThreads, 2) k_scatter(Job j, int level) {
   const int L = level & 1;
   Ctl* ctl = j.ctl;
   const u64 nb = ctl->nbins[L];
-  if (nb == 0) return;
+  if (nb == 0 || call_failed(ctl)) return;
   const u64 ntiles = ctl->ntiles[L];
   const Bin* bins = j.bins[L];
   const u32 RW = RWT ? (u32)RWT : j.RW;
@@ -551,16 +551,21 @@ __global__ void __launch_bounds__(kSThreads, 2) k_scatter(Job j, int level) {
   u32* tbase = (u32*)(smem + lay.tbase);
   u64* gbase = (u64*)(smem + lay.gbase);
   __shared__ u32 scan_scr[kSWarps + 1];
-  __shared__ __align__(8) u64 s_bar;  // completes when a tile's bulk copy has landed
+  __shared__ __align__(8) u64 s_bar;    // completes when a tile's bulk copy has landed
+  __shared__ __align__(8) u64 s_never;  // testing (kInjectWait): a barrier nothing completes
   const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
   const u32 ltmask = lanemask_lt();
   u32 bar_phase = 0;
-  if (tid == 0) mbar_init(&s_bar, 1);
+  if (tid == 0) {
+    mbar_init(&s_bar, 1);
+    mbar_init(&s_never, 1);
+  }
   // per-warp digit counters: counts while ranking, then each warp's offset inside the digit's
   // run; they are zeroed again while the tile is written out
   for (u32 i = tid; i < kSWarps * WSMAX; i += kSThreads) whist[i] = 0;
   const u64 per = lane_tiles(ntiles, j.lanes);
-  bool inject = j.inject != 0 && blockIdx.x == 0 && tid == 0;  // testing: fail one run check
+  bool inject = (j.inject & kInjectRange) && blockIdx.x == 0 && tid == 0;  // testing: fail one run check
+  bool inject_wait = (j.inject & kInjectWait) && blockIdx.x == 0;  // testing: one wait runs out
   __syncthreads();
 
   for (u64 ln = blockIdx.x; ln < j.lanes; ln += gridDim.x) {
@@ -626,15 +631,19 @@ __global__ void __launch_bounds__(kSThreads, 2) k_scatter(Job j, int level) {
           run[q] = (q < D && v < nd) ? sg[v] : 0;
         }
       }
-      // bounded: a bulk copy that has not landed after 2^20 suspended waits is reported (it
-      // cannot be cancelled, so the CTA waits for it once more before it gives up); every
-      // thread takes the same way out
+      // bounded: a bulk copy that has not landed after j.wd_polls suspended waits is reported
+      // (it cannot be cancelled, so the CTA waits for it once more, with the default limit,
+      // before it gives up); every thread takes the same way out
       bool failed = false;
-      if (bulk) failed = !mbar_wait(&s_bar, bar_phase, 1u << 20);
-      else cp_async_wait_all();
+      if (bulk) {
+        failed = !mbar_wait(inject_wait ? &s_never : &s_bar, inject_wait ? 0u : bar_phase, j.wd_polls);
+        inject_wait = false;
+      } else {
+        cp_async_wait_all();
+      }
       if (__syncthreads_or(failed)) {
-        if (tid == 0) atomicOr(&ctl->err, kErrTimeout);
-        mbar_wait(&s_bar, bar_phase, 1u << 20);
+        if (tid == 0) report(ctl, kErrTimeout);
+        mbar_wait(&s_bar, bar_phase, kWaitPolls);
         return;
       }
       if (bulk) bar_phase ^= 1;
@@ -731,7 +740,7 @@ __global__ void __launch_bounds__(kSThreads, 2) k_scatter(Job j, int level) {
           inject = false;
         }
         if (bad) {
-          atomicOr(&ctl->err, kErrInternal);
+          report(ctl, kErrInternal);
           g = kSkip;
         }
         tbase[v] = tb;
@@ -831,7 +840,7 @@ __device__ void push_pieces(const Job& j, u64 begin, u64 c) {
   const u64 np = ceil_div(c, kPieceRecords);
   const u64 idx = atomicAdd(&ctl->npieces, np);
   if (idx + np > j.cap_pieces) {
-    atomicOr(&ctl->err, kErrOverflow);
+    report(ctl, kErrOverflow);
     return;
   }
   for (u64 q = 0; q < np; q++) {
@@ -895,7 +904,7 @@ __global__ void __launch_bounds__(kClsThreads, kClsCtas) k_classify(Job j, int l
   const int L = level & 1, N = L ^ 1;
   Ctl* ctl = j.ctl;
   const u64 nb = ctl->nbins[L];
-  if (nb == 0) return;
+  if (nb == 0 || call_failed(ctl)) return;
   const Bin* bins = j.bins[L];
   constexpr u32 kMaxD = 1u << kWMax;
   __shared__ u32 S[kMaxD];              // inclusive prefix of sub-bin sizes
@@ -936,7 +945,7 @@ __global__ void __launch_bounds__(kClsThreads, kClsCtas) k_classify(Job j, int l
         u64 bv = bbase[v];
         u64 next = v + 1 < nd ? bbase[v + 1] : bin.size;
         if (next < bv || next > bin.size) {  // inconsistent bases (only after a reported error)
-          atomicOr(&ctl->err, kErrInternal);
+          report(ctl, kErrInternal);
           next = bv = min(bv, bin.size);
         }
         const u64 c = next - bv;
@@ -970,7 +979,7 @@ __global__ void __launch_bounds__(kClsThreads, kClsCtas) k_classify(Job j, int l
           const u64 idx = atomicAdd(&ctl->nbins[N], 1ull);
           const u64 bo = atomicAdd(&ctl->base_used[N], (u64)nnd);
           if (idx >= j.cap_bins || bo + nnd > j.cap_base) {
-            atomicOr(&ctl->err, kErrOverflow);
+            report(ctl, kErrOverflow);
           } else {
             Bin nbn = {};
             nbn.begin = rb;
@@ -1044,7 +1053,7 @@ __global__ void __launch_bounds__(kClsThreads, kClsCtas) k_classify(Job j, int l
       const u32 npk = s_npk;
       const u64 base = s_base, tbase = s_tbase;
       const bool ok = base + s_nn <= j.cap_chunks, ok_t = tbase + s_nt <= j.cap_chunks;
-      if (tid == 0 && !(ok && ok_t)) atomicOr(&ctl->err, kErrOverflow);
+      if (tid == 0 && !(ok && ok_t)) report(ctl, kErrOverflow);
       for (u32 q = tid; q < npk; q += kClsThreads) {
         const u32 vf = pk[q], vl = vlast[vf], r = pkr[q];
         const bool tiny = (r & kTinyChunk) != 0;

@@ -109,7 +109,9 @@ def test_launch_counter_starts_and_is_monotone():
 
 def test_inject_flag_validation():
     L = rg.lib()
-    assert L.radix_sort_test_inject(2) == 1
+    assert L.radix_sort_test_inject(4) == 1  # bits 0 (range check) and 1 (wait) only
+    for flags in (1, 2, 3):
+        assert L.radix_sort_test_inject(flags) == 0
     assert L.radix_sort_test_inject(0) == 0
 
 

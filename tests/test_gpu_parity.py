@@ -113,6 +113,42 @@ def test_sort_parity_degenerate(kind):
     np.testing.assert_array_equal(gsort(a, K), oracle.sort(a, K))
 
 
+@pytest.mark.parametrize("R,K", [(16, 8), (8, 8), (24, 16), (32, 8), (16, 16)])
+def test_sort_parity_composite_ties(R, K):
+    """The on-chip sorter's first round ranks records by composite keys: the top key bits
+    below the chunk's shared bits (at most 51 of them) plus the record's position.  Here keys
+    share long prefixes drawn from a pool and differ only in their low 10 bits, so records
+    of one prefix tie in the kept bits and must fall back to whole-key comparisons.  Single
+    chunks (n <= the on-chip limit) and chunks formed after a distribution level both occur;
+    a pool of few prefixes makes buckets larger than the enumeration limit (general rounds)."""
+    rng = np.random.default_rng(R * 13 + K)
+    cm = rg.chunk_records(R)
+    for n, npref in ((cm, 400), (cm - 7, 20), (3000, 3000), (250_000, 30_000), (250_000, 40)):
+        a = rand(rng, n, R, K)
+        pool = rng.integers(0, 256, size=(npref, K), dtype=np.uint8)
+        keys = pool[rng.integers(0, npref, n)]
+        low = rng.integers(0, 1 << 10, n)
+        keys[:, 0] = (low & 0xFF).astype(np.uint8)
+        keys[:, 1] = (keys[:, 1] & 0xFC) | (low >> 8).astype(np.uint8)
+        a[:, :K] = keys
+        np.testing.assert_array_equal(gsort(a, K), oracle.sort(a, K), err_msg=f"n={n} prefixes={npref}")
+
+
+@pytest.mark.parametrize("n,R,K", [(300_007, 16, 8), (4_000_000, 16, 8), (1_000_003, 24, 16)])
+def test_sort_parity_sm_limit(n, R, K):
+    """Grids capped to 19 SMs (the SM-count sweep): fewer lanes, so every histogram and scatter
+    CTA walks more tiles and more bins, and fewer chunk CTAs take more chunks each."""
+    rng = np.random.default_rng(n + R)
+    a = rand(rng, n, R, K)
+    old = rg.get_plan()
+    try:
+        rg.set_plan(sm_limit=19)
+        got = gsort(a, K)
+    finally:
+        rg.set_plan(**old)
+    np.testing.assert_array_equal(got, oracle.sort(a, K))
+
+
 @pytest.mark.parametrize("R,K,pattern", [(16, 8, "90"), (16, 8, "55"), (16, 8, "two"), (16, 8, "zero"),
                                          (16, 8, "ones"), (24, 16, "90"), (24, 16, "ones"), (16, 5, "90"),
                                          (8, 8, "97"), (64, 16, "two")])

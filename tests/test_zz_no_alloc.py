@@ -28,7 +28,9 @@ def test_noalloc_matches_radix_sort_on_two_calls_in_a_row():
     torch = pytest.importorskip("torch")
     L = rg.lib()
     stream = torch.cuda.current_stream()
-    for call, (n, rec, key) in enumerate([(1_000_003, 16, 8), (700_001, 24, 16)]):
+    # two sorts that distribute before sorting on chip, then one small enough for a single chunk
+    cases = [(1_000_003, 16, 8), (700_001, 24, 16), (1_000, 16, 8)]
+    for call, (n, rec, key) in enumerate(cases):
         rng = np.random.default_rng(100 + call)
         a = rng.integers(0, 256, size=(n, rec), dtype=np.uint8)
         want = torch.from_numpy(a).cuda()
@@ -36,9 +38,15 @@ def test_noalloc_matches_radix_sort_on_two_calls_in_a_row():
         got = torch.from_numpy(a).cuda()
         tmp = torch.empty_like(got)
         status = torch.full((1,), 0xFFFF, dtype=torch.int32, device="cuda")
+        torch.cuda.synchronize()
+        free_before = torch.cuda.mem_get_info()[0]
         rc = L.radix_sort_noalloc(got.data_ptr(), tmp.data_ptr(), n, rec, key, status.data_ptr(),
                                   ctypes.c_void_p(stream.cuda_stream))
         assert rc == RS_OK
         torch.cuda.synchronize()
+        if call > 0:
+            # the first call on a device may load the array's module (that reserves its memory);
+            # every later call takes no device memory at all
+            assert torch.cuda.mem_get_info()[0] == free_before, f"call {call} took device memory"
         assert int(status.item()) == 0
         assert torch.equal(got, want), f"call {call}: output differs from radix_sort"

@@ -86,21 +86,25 @@ __device__ bool scan_counts(const ChunkCtx<KW, RWT>& c, u32 nd, u32 big = 0xffff
   const u32 words = nd >> 1;
   const u32 per = (words + kCThreads - 1) / kCThreads;
   const u32 w0 = min(words, tid * per), w1 = min(words, w0 + per);
-  // four words per thread (a full window's counters): one 16-byte access instead of four
-  // accesses of consecutive words per lane, which meet a 4-way bank conflict
+  // a full window's counters: 16-byte accesses (four words each) instead of accesses of
+  // consecutive words per lane, which meet a 4-way bank conflict
+  constexpr u32 kV = kCntWords / kCThreads / 4 > 0 ? kCntWords / kCThreads / 4 : 1;
   u32 sum = 0, mx = 0;
-  uint4 v4 = make_uint4(0, 0, 0, 0);
-  const bool vec = per == 4 && w1 - w0 == 4;
+  uint4 v4[kV];
+  const bool vec = per == 4 * kV && w1 - w0 == 4 * kV;
   auto take = [&](u32 x) {
     sum += (x & 0xffffu) + (x >> 16);
     mx = max(mx, max(x & 0xffffu, x >> 16));
   };
   if (vec) {
-    v4 = *reinterpret_cast<const uint4*>(c.cnt + w0);
-    take(v4.x);
-    take(v4.y);
-    take(v4.z);
-    take(v4.w);
+#pragma unroll
+    for (u32 q = 0; q < kV; q++) {
+      v4[q] = reinterpret_cast<const uint4*>(c.cnt + w0)[q];
+      take(v4[q].x);
+      take(v4[q].y);
+      take(v4[q].z);
+      take(v4[q].w);
+    }
   } else {
     for (u32 w = w0; w < w1; w++) take(c.cnt[w]);
   }
@@ -131,12 +135,15 @@ __device__ bool scan_counts(const ChunkCtx<KW, RWT>& c, u32 nd, u32 big = 0xffff
       run = hi + (v >> 16);
       return w;
     };
-    uint4 o;
-    o.x = starts(v4.x);
-    o.y = starts(v4.y);
-    o.z = starts(v4.z);
-    o.w = starts(v4.w);
-    *reinterpret_cast<uint4*>(c.cnt + w0) = o;
+#pragma unroll
+    for (u32 q = 0; q < kV; q++) {
+      uint4 o;
+      o.x = starts(v4[q].x);
+      o.y = starts(v4[q].y);
+      o.z = starts(v4[q].z);
+      o.w = starts(v4[q].w);
+      reinterpret_cast<uint4*>(c.cnt + w0)[q] = o;
+    }
   } else {
     for (u32 w = w0; w < w1; w++) {
       const u32 v = c.cnt[w];
@@ -449,11 +456,13 @@ __global__ void __launch_bounds__(kCThreads, kChunkCtas) k_chunk(Job j) {
   c.stack_cap = m / (kEsMax + 1) + 2;
   c.cnt = (u32*)(smem + lay.cnt);
   __shared__ Chunk s_ch;
-  __shared__ u64 s_t;
+  __shared__ __align__(16) Chunk s_next;  // the next ticket's descriptor, copied in by cp.async
+  __shared__ u64 s_t, s_nt;
   __shared__ u32 s_top;
-  __shared__ __align__(8) u64 s_bar;  // completes when a chunk's bulk copy has landed
-  const int tid = threadIdx.x;
+  __shared__ __align__(8) u64 s_bar[kCWarps];  // bar w: warp w's strip of the chunk has landed
+  const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
   constexpr u32 kIdxMask = (1u << kIdxBits) - 1u;
+  constexpr u32 kStrip = kChunkItems * 32;  // records of a warp strip (kCWarps strips cover chunk_max)
   u32 bar_phase = 0;
 
   // thread 0: publish ticket t with its descriptor `raw` (an unusable one is reported, not
@@ -483,8 +492,8 @@ __global__ void __launch_bounds__(kCThreads, kChunkCtas) k_chunk(Job j) {
     return t_next++;
   };
   for (u32 i = tid; i < (u32)kCntWords; i += kCThreads) c.cnt[i] = 0;
+  if (tid < kCWarps) mbar_init(&s_bar[tid], 1);
   if (tid == 0) {
-    mbar_init(&s_bar, 1);
     const u64 t = take();
     Chunk raw = {};
     if (t < nch) raw = j.chunks[t];
@@ -496,52 +505,69 @@ __global__ void __launch_bounds__(kCThreads, kChunkCtas) k_chunk(Job j) {
     const Chunk ch = s_ch;
     const u32 sz = ch.size;
     const bool in_place = !(ch.flags & kChSrcTmp), copy_only = (ch.flags & kChCopyOnly) != 0;
-    // the records come in by one bulk copy when they start on a 16-byte boundary (an even
-    // word count per record: always), else by 16- or 8-byte copies of every thread
+    // the records come in by bulk copies when they start on a 16-byte boundary (an even word
+    // count per record: always), one per warp strip of kStrip records, each completing on its
+    // own barrier; else by 16- or 8-byte copies of every thread
     const u64* src = j.buf[in_place ? 0 : 1] + ch.begin * RW;
     const u32 bytes = sz * RW * 8;
     const bool load = sz && !(copy_only && in_place);
     const bool bulk = load && ((((uintptr_t)src) | bytes) & 15) == 0;
     if (load && !bulk) load_words_async<kCThreads>(stage, src, (u64)sz * RW);
-    if (bulk && tid == 0) {
+    if (bulk && lane == 0) {
+      // (strip boundaries are multiples of kStrip records: 16-byte aligned, as is the chunk's end)
+      const u32 a = warp * kStrip, e = min(sz, a + kStrip);
       fence_proxy_async_smem();  // the last chunk's reads of the stage are done (barrier)
-      bulk_load(stage, src, bytes, &s_bar);
+      if (e > a) bulk_load(stage + (u64)a * RW, src + (u64)a * RW, (e - a) * RW * 8, &s_bar[warp]);
+      else mbar_arrive(&s_bar[warp]);
     }
-    u64 nt = 0;
-    Chunk nraw = {};
-    if (tid == 0) {  // the next ticket and its descriptor (published after the wait)
-      nt = take();
-      if (nt < nch) nraw = j.chunks[nt];
+    if (tid == 0) {  // the next ticket; its descriptor comes into s_next (published after the wait)
+      const u64 nt = take();
+      s_nt = nt;
+      static_assert(sizeof(Chunk) == 32, "a descriptor is two 16-byte copies");
+      if (nt < nch) {
+        cp_async16(&s_next, j.chunks + nt);
+        cp_async16(reinterpret_cast<char*>(&s_next) + 16, reinterpret_cast<const char*>(j.chunks + nt) + 16);
+      }
+      cp_async_commit();
     }
-    // bounded wait (the copy cannot be cancelled: after a timeout the CTA still waits for it,
-    // with the default limit, before it leaves)
-    bool failed = false;
-    if (bulk) failed = !mbar_wait(&s_bar, bar_phase, j.wd_polls);
-    else cp_async_wait_all();
-    if (__syncthreads_or(failed)) {
-      if (tid == 0) report(ctl, kErrTimeout);
-      mbar_wait(&s_bar, bar_phase, kWaitPolls);
-      return;
-    }
-    if (bulk) bar_phase ^= 1;
-    if (tid == 0) fetch(nt, nraw);  // every thread has read s_ch and s_t (barrier above)
-
     u64* dst = j.buf[0] + ch.begin * RW;
     DigitSpec dig = {};
     u32 p = ch.p;
     bool sort = sz && !copy_only;
-    if (sort) {
-      if (p) {  // shared bits known from the level that produced the chunk
-        dig = window_below(p, sz);
-        if (ch.sb) {
-          dig.sb = ch.sb;
-          dig.plo = p;
-          dig.pw = ch.pw;
-          dig.v0 = ch.v0;
-          dig.w = p > (u32)kWinBits - ch.sb ? (u32)kWinBits - ch.sb : p;
-          dig.lo = p - dig.w;
-        }
-      } else {
+    if (sort && p) {  // shared bits known from the level that produced the chunk
+      dig = window_below(p, sz);
+      if (ch.sb) {
+        dig.sb = ch.sb;
+        dig.plo = p;
+        dig.pw = ch.pw;
+        dig.v0 = ch.v0;
+        dig.w = p > (u32)kWinBits - ch.sb ? (u32)kWinBits - ch.sb : p;
+        dig.lo = p - dig.w;
+      }
+    }
+    // bounded waits, each warp for its own strip (a copy cannot be cancelled: after a timeout
+    // the CTA still waits for every strip, with the default limit, before it leaves)
+    bool failed = false;
+    if (bulk) failed = !mbar_wait(&s_bar[warp], bar_phase, j.wd_polls);
+    if (!bulk) cp_async_wait_all();
+    auto give_up = [&]() {
+      if (tid == 0) report(ctl, kErrTimeout);
+      if (bulk) mbar_wait(&s_bar[warp], bar_phase, kWaitPolls);
+    };
+    // the first round counts each warp's own strip as soon as it has landed; every other path
+    // reads the whole chunk and waits for all strips first
+    const bool strips = bulk && sort && p && sz > (u32)kEsMax;
+    if (!strips) {
+      if (__syncthreads_or(failed)) {
+        give_up();
+        return;
+      }
+      if (bulk) bar_phase ^= 1;
+      if (tid == 0) {  // every thread has read s_ch and s_t (barrier above)
+        cp_async_wait_all();
+        fetch(s_nt, s_next);
+      }
+      if (sort && !p) {
         p = range_top_bit(c, 0, sz, false);  // (ends with a barrier)
         sort = p != 0;
         dig = window_below(p, sz);
@@ -555,7 +581,7 @@ __global__ void __launch_bounds__(kCThreads, kChunkCtas) k_chunk(Job j) {
       u32 held[kChunkItems];  // (digit << 16) | rank among the digit's records counted before
 #pragma unroll
       for (int k = 0; k < kChunkItems; k++) {
-        const u32 i = tid + k * kCThreads;
+        const u32 i = warp * kStrip + k * 32 + lane;  // (this warp's strip)
         held[k] = 0xffffffffu;
         ck[k] = 0;
         if (i < sz) {
@@ -566,7 +592,19 @@ __global__ void __launch_bounds__(kCThreads, kChunkCtas) k_chunk(Job j) {
         }
       }
       if (tid == 0) s_top = 0;
-      __syncthreads();
+      if (strips) {
+        if (__syncthreads_or(failed)) {
+          give_up();
+          return;
+        }
+        bar_phase ^= 1;
+        if (tid == 0) {  // every thread has read s_ch and s_t (barrier above)
+        cp_async_wait_all();
+        fetch(s_nt, s_next);
+      }
+      } else {
+        __syncthreads();
+      }
       const u32 nd = cs.dmask + 1;
       const bool big = scan_counts(c, nd < 2 ? 2 : nd, (u32)kEsMax);  // (ends with a barrier)
       if (!big) {
@@ -603,9 +641,9 @@ __global__ void __launch_bounds__(kCThreads, kChunkCtas) k_chunk(Job j) {
               const u64* sp = stage + (u64)r * RW;
               u64* dp = dst + (u64)pos * RW;
               if (RW == 2)
-                __stcs(reinterpret_cast<ulonglong2*>(dp), *reinterpret_cast<const ulonglong2*>(sp));
+                *reinterpret_cast<ulonglong2*>(dp) = *reinterpret_cast<const ulonglong2*>(sp);
               else
-                __stcs(dp, sp[0]);
+                *dp = sp[0];
             } else {
               placed[k] = (pos << 16) | r;
             }
@@ -623,7 +661,7 @@ __global__ void __launch_bounds__(kCThreads, kChunkCtas) k_chunk(Job j) {
 #pragma unroll
         for (int k = 0; k < kChunkItems; k++)
           if (held[k] != 0xffffffffu)
-            c.out[c.count_of(held[k] >> 16) + (held[k] & 0xffffu)] = (u16)(tid + k * kCThreads);
+            c.out[c.count_of(held[k] >> 16) + (held[k] & 0xffffu)] = (u16)(warp * kStrip + k * 32 + lane);
         __syncthreads();
         finish_round(c, 0, sz, dig, &s_top);
         while (s_top) {  // s_top is final after the barrier that ends every round
@@ -668,7 +706,6 @@ __global__ void __launch_bounds__(kCThreads, kChunkCtas) k_chunk(Job j) {
       } else {
         // whole warps write consecutive records: lane k * P + piece moves one piece (16 bytes
         // if RW is even, else 8) of record s0 + k (P <= 32: records are at most 256 bytes)
-        const int lane = tid & 31, warp = tid >> 5;
         const bool pairs = (RW & 1) == 0;
         const u32 P = pairs ? RW >> 1 : RW, rpw = 32 / P;
         const u32 k = lane / P, piece = lane - k * P;

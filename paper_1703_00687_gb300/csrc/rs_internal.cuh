@@ -293,6 +293,10 @@ __device__ __forceinline__ void bulk_load(void* dst, const void* src, unsigned b
                "l"(src), "r"(bytes), "r"(smem_u32(bar))
                : "memory");
 }
+// One arrival on the barrier without a copy (completes a phase that has nothing to load).
+__device__ __forceinline__ void mbar_arrive(u64* bar) {
+  asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(smem_u32(bar)) : "memory");
+}
 // Wait until the barrier's phase `parity` has completed, at most `tries` waits (each one
 // suspends the thread for a bounded time); false if it did not complete.
 __device__ __forceinline__ bool mbar_wait(u64* bar, unsigned parity, unsigned tries) {

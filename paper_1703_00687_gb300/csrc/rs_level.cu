@@ -551,15 +551,13 @@ __global__ void __launch_bounds__(kSThreads, 2) k_scatter(Job j, int level) {
   u32* tbase = (u32*)(smem + lay.tbase);
   u64* gbase = (u64*)(smem + lay.gbase);
   __shared__ u32 scan_scr[kSWarps + 1];
-  __shared__ __align__(8) u64 s_bar;    // completes when a tile's bulk copy has landed
-  __shared__ __align__(8) u64 s_never;  // testing (kInjectWait): a barrier nothing completes
+  __shared__ __align__(8) u64 s_bar[kSWarps];  // bar w: warp w's strip of a tile has landed
+  __shared__ __align__(8) u64 s_never;          // testing (kInjectWait): a barrier nothing completes
   const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
   const u32 ltmask = lanemask_lt();
   u32 bar_phase = 0;
-  if (tid == 0) {
-    mbar_init(&s_bar, 1);
-    mbar_init(&s_never, 1);
-  }
+  if (tid < kSWarps) mbar_init(&s_bar[tid], 1);
+  if (tid == 0) mbar_init(&s_never, 1);
   // per-warp digit counters: counts while ranking, then each warp's offset inside the digit's
   // run; they are zeroed again while the tile is written out
   for (u32 i = tid; i < kSWarps * WSMAX; i += kSThreads) whist[i] = 0;
@@ -607,16 +605,21 @@ __global__ void __launch_bounds__(kSThreads, 2) k_scatter(Job j, int level) {
       const u32 cnt = (u32)min((u64)T, size - r0);
       u64* dstb = j.buf[parity ^ 1];
 
-      // the tile comes in by one bulk copy when it starts on a 16-byte boundary (an even word
-      // count per record: always), else by 16- or 8-byte copies of every thread
+      // the tile comes in by bulk copies when it starts on a 16-byte boundary (an even word
+      // count per record: always), one per warp strip, each completing on its own barrier so
+      // that a warp starts ranking as soon as its strip has landed; else by 16- or 8-byte
+      // copies of every thread
       const u64* src = j.buf[parity] + (begin + r0) * RW;
       const u32 bytes = cnt * RW * 8;
       const bool bulk = ((((uintptr_t)src) | bytes) & 15) == 0;
       if (!bulk) {
         load_words_async<kSThreads>(stage, src, (u64)cnt * RW);
-      } else if (tid == 0) {
+      } else if (lane == 0) {
+        // (strip boundaries are multiples of PW records: 16-byte aligned, as is the tile's end)
+        const u32 a = warp * PW, e = min(cnt, a + PW);
         fence_proxy_async_smem();  // the last tile's reads of the stage are done (barrier)
-        bulk_load(stage, src, bytes, &s_bar);
+        if (e > a) bulk_load(stage + (u64)a * RW, src + (u64)a * RW, (e - a) * RW * 8, &s_bar[warp]);
+        else mbar_arrive(&s_bar[warp]);
       }
       // the lane's next tile of this bin comes into L2 while this one is processed
       if (tid == 0 && t + 1 < t1 && r0 + T < size)
@@ -631,26 +634,27 @@ __global__ void __launch_bounds__(kSThreads, 2) k_scatter(Job j, int level) {
           run[q] = (q < D && v < nd) ? sg[v] : 0;
         }
       }
-      // bounded: a bulk copy that has not landed after j.wd_polls suspended waits is reported
-      // (it cannot be cancelled, so the CTA waits for it once more, with the default limit,
-      // before it gives up); every thread takes the same way out
+      // bounded: a strip that has not landed after j.wd_polls suspended waits is reported after
+      // the ranking (its warp ranks nothing; the copies cannot be cancelled, so the CTA waits
+      // for every strip once more, with the default limit, before it gives up); every thread
+      // takes the same way out
       bool failed = false;
       if (bulk) {
-        failed = !mbar_wait(inject_wait ? &s_never : &s_bar, inject_wait ? 0u : bar_phase, j.wd_polls);
+        failed = !mbar_wait(inject_wait && warp == 0 ? &s_never : &s_bar[warp], inject_wait && warp == 0 ? 0u : bar_phase,
+                            j.wd_polls);
         inject_wait = false;
+        failed = __any_sync(kFull, failed);  // (the whole warp skips its strip)
       } else {
         cp_async_wait_all();
+        __syncthreads();
       }
-      if (__syncthreads_or(failed)) {
-        if (tid == 0) report(ctl, kErrTimeout);
-        mbar_wait(&s_bar, bar_phase, kWaitPolls);
-        return;
-      }
-      if (bulk) bar_phase ^= 1;
 
       // stable rank: warp w owns records [w*PW, (w+1)*PW), visited in order
       u32 packed[IT];
-      if (cnt == T) {
+      if (failed) {
+#pragma unroll
+        for (int it = 0; it < IT; it++) packed[it] = 0xffffffffu;
+      } else if (cnt == T) {
         // first every item's digit and peers (independent of each other), then the counters
         u32 dg[IT], pr[IT];
         if (!dom) {  // (the two loops differ in the bucket function only)
@@ -693,7 +697,13 @@ __global__ void __launch_bounds__(kSThreads, 2) k_scatter(Job j, int level) {
           packed[it] = valid ? ((old + before) | (d << 16)) : 0xffffffffu;
         }
       }
-      __syncthreads();
+      if (__syncthreads_or(failed)) {
+        if (tid == 0) report(ctl, kErrTimeout);
+        if (lane == 0) mbar_wait(&s_bar[warp], bar_phase, kWaitPolls);
+        __syncwarp();
+        return;
+      }
+      if (bulk) bar_phase ^= 1;
       // Thread tid owns digits [D*tid, D*tid + D): it turns their per-warp counts into each
       // warp's offset inside the digit's run (two 16-bit counters per 32-bit access), then one
       // block scan of the threads' totals gives the digits' first slots in the tile.

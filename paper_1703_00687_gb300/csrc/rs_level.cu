@@ -19,6 +19,8 @@
 // A bin that a sample showed to be mostly one key (kBinDom) is counted and scattered with
 // that key's digit split in three (below, equal, above; see bucket_of), and classify
 // finishes the equal part at once: heavy keys are not moved again at later levels.
+#include <algorithm>
+
 #include "rs_internal.cuh"
 
 namespace rsg {
@@ -471,9 +473,11 @@ constexpr int kSThreads = 256;  // threads of a scatter CTA
 constexpr int kSWarps = kSThreads / 32;
 
 // Shared memory of k_scatter: T records, per-warp 16-bit digit counters (row stride 2^wmax),
-// the tile's permutation, per-digit counts / run bases / global bases.
+// the tile's permutation (sharing its room with one byte per warp and bucket, used while
+// ranking to find the lanes that share a bucket: see rank_item), per-digit counts / run bases
+// / global bases.
 struct ScatterLayout {
-  size_t stage, whist, slot, tbase, gbase, total;
+  size_t stage, whist, slot, tbase, gbase, winner, total;
 };
 
 __host__ __device__ inline ScatterLayout scatter_layout(u32 T, u32 RW, u32 wmax) {
@@ -482,24 +486,13 @@ __host__ __device__ inline ScatterLayout scatter_layout(u32 T, u32 RW, u32 wmax)
   size_t o = 0;
   s.stage = o; o += (size_t)T * RW * 8;
   s.whist = o; o += (size_t)kSWarps * nd * 2;
-  s.slot = o; o += (size_t)T * 4;
+  // (the winner bytes are used only while ranking, before the permutation is written)
+  s.slot = s.winner = o; o += std::max((size_t)T * 4, (size_t)kSWarps * nd);
   o = (o + 15) & ~(size_t)15;
   s.tbase = o; o += nd * 4;
   s.gbase = o; o += nd * 8;
   s.total = (o + 127) & ~(size_t)127;
   return s;
-}
-
-// Lanes of the warp whose digit equals this lane's (d has W significant bits): one vote per
-// digit bit.  Lanes with valid == false get a mask of their own.
-__device__ __forceinline__ u32 peers_of(u32 d, u32 W, bool valid) {
-  u32 peers = __ballot_sync(kFull, valid);
-  for (u32 b = 0; b < W; b++) {
-    const bool bit = (d >> b) & 1u;
-    const u32 v = __ballot_sync(kFull, bit);
-    peers &= bit ? v : ~v;
-  }
-  return valid ? peers : (1u << (threadIdx.x & 31));
 }
 
 // Digit of a staged record.  No key mask is needed: a digit window never reaches past the key.
@@ -526,8 +519,9 @@ constexpr u64 kSkip = ~0ull;  // gbase of a digit whose run would leave its bin
 // which the CTA keeps in registers: no tile waits for another.
 //
 // Per tile of T = kSThreads * IT records: the records are staged in shared memory; warp w
-// ranks its strip of records in order (peer masks by one vote per digit bit, per-warp 16-bit
-// counters), so the order inside a digit is the input order (stable); the digit counts are
+// ranks its strip of records in order (lanes sharing a bucket found through a per-warp byte
+// per bucket, per-warp 16-bit counters), so the order inside a digit is the input order
+// (stable); the digit counts are
 // scanned; then the tile is written in digit order, so consecutive threads write consecutive
 // records of a run with 16-byte streaming stores.
 template <int KW, int RWT, int IT>
@@ -547,6 +541,7 @@ __global__ void __launch_bounds__(kSThreads, 2) k_scatter(Job j, int level) {
   extern __shared__ __align__(16) unsigned char smem[];
   u64* stage = (u64*)(smem + lay.stage);
   u16* whist = (u16*)(smem + lay.whist);
+  u8* winner = (u8*)(smem + lay.winner);
   u32* slotw = (u32*)(smem + lay.slot);  // per output slot: staged record | digit << 16
   u32* tbase = (u32*)(smem + lay.tbase);
   u64* gbase = (u64*)(smem + lay.gbase);
@@ -649,52 +644,57 @@ __global__ void __launch_bounds__(kSThreads, 2) k_scatter(Job j, int level) {
         __syncthreads();
       }
 
+      // Stable rank of one item (one record per lane, lanes in record order) among the warp's
+      // records of its bucket: the count before this item (per-warp counter) + the lanes below
+      // it with the same bucket.  The lanes sharing a bucket are found without a vote per
+      // digit bit: every lane writes its id into its bucket's byte, and all lanes of a bucket
+      // read back the same winner.  With 2^9 buckets and 32 lanes most items have no shared
+      // bucket (every lane reads its own id back: one vote tells); otherwise lanes are grouped
+      // by their winner's id, which takes 5 votes.  Lanes without a record (valid = false)
+      // write nothing and form groups of their own.  Returns (rank | bucket << 16), or all ones.
+      u8* wn = winner + warp * WS;
+      auto rank_item = [&](u32 d, bool valid) -> u32 {
+        if (valid) wn[d] = (u8)lane;
+        __syncwarp();
+        const u32 w = valid ? (u32)wn[d] : (u32)lane, old = valid ? (u32)wh[d] : 0u;
+        u32 peers = 1u << lane;
+        if (__any_sync(kFull, w != (u32)lane)) {
+          u32 x = 0;
+#pragma unroll
+          for (int b = 0; b < 5; b++) {
+            const u32 v = __ballot_sync(kFull, (w >> b) & 1u);
+            x |= v ^ (0u - ((w >> b) & 1u));
+          }
+          peers = ~x;
+        }
+        const u32 before = __popc(peers & ltmask);
+        __syncwarp();  // (every lane has read the bucket's byte and counter)
+        if (valid && before == 0) wh[d] = (u16)(old + __popc(peers));
+        return valid ? ((old + before) | (d << 16)) : 0xffffffffu;
+      };
       // stable rank: warp w owns records [w*PW, (w+1)*PW), visited in order
       u32 packed[IT];
       if (failed) {
 #pragma unroll
         for (int it = 0; it < IT; it++) packed[it] = 0xffffffffu;
       } else if (cnt == T) {
-        // first every item's digit and peers (independent of each other), then the counters
-        u32 dg[IT], pr[IT];
+        // first every item's bucket, then the ranks
+        u32 dg[IT];
         if (!dom) {  // (the two loops differ in the bucket function only)
 #pragma unroll
-          for (int it = 0; it < IT; it++) {
-            dg[it] = staged_digit<KW>(stage + (u64)(warp * PW + it * 32 + lane) * RW, lo, W);
-            pr[it] = peers_of(dg[it], W, true);
-          }
+          for (int it = 0; it < IT; it++) dg[it] = staged_digit<KW>(stage + (u64)(warp * PW + it * 32 + lane) * RW, lo, W);
         } else {
 #pragma unroll
-          for (int it = 0; it < IT; it++) {
-            dg[it] = bucket(stage + (u64)(warp * PW + it * 32 + lane) * RW);
-            pr[it] = peers_of(dg[it], BW, true);
-          }
+          for (int it = 0; it < IT; it++) dg[it] = bucket(stage + (u64)(warp * PW + it * 32 + lane) * RW);
         }
 #pragma unroll
-        for (int it = 0; it < IT; it++) {
-          const u32 d = dg[it], peers = pr[it];
-          const u32 before = __popc(peers & ltmask);
-          const u32 old = wh[d];
-          __syncwarp();
-          if (before == 0) wh[d] = (u16)(old + __popc(peers));
-          __syncwarp();
-          packed[it] = (old + before) | (d << 16);
-        }
+        for (int it = 0; it < IT; it++) packed[it] = rank_item(dg[it], true);
       } else {
 #pragma unroll
         for (int it = 0; it < IT; it++) {
           const u32 r = warp * PW + it * 32 + lane;
           const bool valid = r < cnt;
-          u32 d = 0;
-          if (valid) d = bucket(stage + (u64)r * RW);
-          const u32 peers = peers_of(d, BW, valid);
-          const u32 before = __popc(peers & ltmask);
-          u32 old = 0;
-          if (valid) old = wh[d];
-          __syncwarp();
-          if (valid && before == 0) wh[d] = (u16)(old + __popc(peers));
-          __syncwarp();
-          packed[it] = valid ? ((old + before) | (d << 16)) : 0xffffffffu;
+          packed[it] = rank_item(valid ? bucket(stage + (u64)r * RW) : 0u, valid);
         }
       }
       if (__syncthreads_or(failed)) {

@@ -363,6 +363,10 @@ __device__ __forceinline__ void load_words_async(u64* dst, const u64* src, u64 w
 }
 
 
+// Shared memory of k_hist: two buffers of a tile's keys (tile t+1 streams in while tile t
+// is counted).
+__host__ __device__ inline size_t hist_smem_bytes_for(u32 T, u32 KW) { return 2ull * T * KW * 8; }
+
 // ------------------------------------------------------------------ launch helpers
 // Host-side launchers implemented in the kernel translation units.  Each returns the
 // number of kernels it launched (or -1 on a launch error).

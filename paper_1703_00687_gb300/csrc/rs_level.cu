@@ -11,16 +11,14 @@
 //               if not, marks a bin of equal keys finished, and turns counts into bases.
 //               It counts per lane (a contiguous range of the level's tiles), and the last
 //               CTA of a bin also turns every lane's counts into that lane's run starts.
-//   k_scatter   tile-wise stable scatter, lane by lane: a tile's destinations follow from its
-//               lane's run starts and the lane's earlier tiles (no CTA waits for another).
+//   k_scatter   (rs_scatter.cu) tile-wise stable scatter, lane by lane: a tile's destinations
+//               follow from its lane's run starts and the lane's earlier tiles.
 //   k_classify  sub-bin classification, chunk packing (chunks of at most kTinyMax records go
 //               to the tiny list), the next level's bin list.
 //
 // A bin that a sample showed to be mostly one key (kBinDom) is counted and scattered with
 // that key's digit split in three (below, equal, above; see bucket_of), and classify
 // finishes the equal part at once: heavy keys are not moved again at later levels.
-#include <algorithm>
-
 #include "rs_internal.cuh"
 
 namespace rsg {
@@ -291,9 +289,6 @@ __device__ void finish_bin(const Job& j, int L, u64 b, int mode) {
   }
 }
 
-// Shared memory of k_hist: two buffers of a tile's keys (tile t+1 streams in while tile t
-// is counted).
-__host__ __device__ inline size_t hist_smem_bytes_for(u32 T, u32 KW) { return 2ull * T * KW * 8; }
 
 
 template <int KW>
@@ -466,354 +461,6 @@ __global__ void __launch_bounds__(kThreads, 2) k_hist(Job j, int level, int mode
     __syncthreads();  // buffer `buf` is refilled by the next issue
   }
   if (counted) flush(cur);
-}
-
-// --------------------------------------------------------------------- scatter
-constexpr int kSThreads = 256;  // threads of a scatter CTA
-constexpr int kSWarps = kSThreads / 32;
-
-// Shared memory of k_scatter: T records, per-warp 16-bit digit counters (row stride 2^wmax),
-// the tile's permutation (sharing its room with one byte per warp and bucket, used while
-// ranking to find the lanes that share a bucket: see rank_item), per-digit counts / run bases
-// / global bases.
-struct ScatterLayout {
-  size_t stage, whist, slot, tbase, gbase, winner, total;
-};
-
-__host__ __device__ inline ScatterLayout scatter_layout(u32 T, u32 RW, u32 wmax) {
-  ScatterLayout s;
-  const size_t nd = (size_t)1 << wmax;
-  size_t o = 0;
-  s.stage = o; o += (size_t)T * RW * 8;
-  s.whist = o; o += (size_t)kSWarps * nd * 2;
-  // (the winner bytes are used only while ranking, before the permutation is written)
-  s.slot = s.winner = o; o += std::max((size_t)T * 4, (size_t)kSWarps * nd);
-  o = (o + 15) & ~(size_t)15;
-  s.tbase = o; o += nd * 4;
-  s.gbase = o; o += nd * 8;
-  s.total = (o + 127) & ~(size_t)127;
-  return s;
-}
-
-// Digit of a staged record.  No key mask is needed: a digit window never reaches past the key.
-template <int KW>
-__device__ __forceinline__ u32 staged_digit(const u64* rec, u32 lo, u32 W) {
-  Key<KW> k;
-  k.w[0] = rec[0];
-  if (KW == 2) k.w[KW - 1] = rec[1];
-  return digit_of<KW>(k, lo, W);
-}
-
-// Digits per thread in the scatter's prefix pass: nd / kSThreads, at least 2 (the per-warp
-// counters are read two at a time).
-__device__ __forceinline__ u32 digits_per_thread(u32 nd) { return nd > 2u * kSThreads ? nd / kSThreads : 2u; }
-
-constexpr u64 kSkip = ~0ull;  // gbase of a digit whose run would leave its bin
-
-// Stable scatter of every large bin of the level into the other buffer.  The level's tiles
-// are split into the same lanes as in the histogram pass (contiguous tile ranges); a CTA
-// takes its lanes in turn and walks each lane's tiles in order.  The histogram pass left,
-// for every (lane, bin) segment and digit, where the segment's records of that digit start
-// (bucket base + the digit's records in the bin's earlier lanes), so a tile's destinations
-// are known from those starts plus the digit counts of the lane's earlier tiles of the bin,
-// which the CTA keeps in registers: no tile waits for another.
-//
-// Per tile of T = kSThreads * IT records: the records are staged in shared memory; warp w
-// ranks its strip of records in order (lanes sharing a bucket found through a per-warp byte
-// per bucket, per-warp 16-bit counters), so the order inside a digit is the input order
-// (stable); the digit counts are
-// scanned; then the tile is written in digit order, so consecutive threads write consecutive
-// records of a run with 16-byte streaming stores.
-template <int KW, int RWT, int IT>
-__global__ void __launch_bounds__(kSThreads, 2) k_scatter(Job j, int level) {
-  const int L = level & 1;
-  Ctl* ctl = j.ctl;
-  const u64 nb = ctl->nbins[L];
-  if (nb == 0 || call_failed(ctl)) return;
-  const u64 ntiles = ctl->ntiles[L];
-  const Bin* bins = j.bins[L];
-  const u32 RW = RWT ? (u32)RWT : j.RW;
-  constexpr u32 T = kSThreads * IT;
-  constexpr u32 PW = T / kSWarps;  // records per warp strip
-  constexpr u32 kDigitsPerThread = (1u << kWMax) / kSThreads;
-  const u32 WSMAX = 1u << j.wmax;  // room for the per-warp counters: kSWarps rows of 2^wmax
-  const ScatterLayout lay = scatter_layout(T, RW, j.wmax);
-  extern __shared__ __align__(16) unsigned char smem[];
-  u64* stage = (u64*)(smem + lay.stage);
-  u16* whist = (u16*)(smem + lay.whist);
-  u8* winner = (u8*)(smem + lay.winner);
-  u32* slotw = (u32*)(smem + lay.slot);  // per output slot: staged record | digit << 16
-  u32* tbase = (u32*)(smem + lay.tbase);
-  u64* gbase = (u64*)(smem + lay.gbase);
-  __shared__ u32 scan_scr[kSWarps + 1];
-  __shared__ __align__(8) u64 s_bar[kSWarps];  // bar w: warp w's strip of a tile has landed
-  __shared__ __align__(8) u64 s_never;          // testing (kInjectWait): a barrier nothing completes
-  const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
-  const u32 ltmask = lanemask_lt();
-  u32 bar_phase = 0;
-  if (tid < kSWarps) mbar_init(&s_bar[tid], 1);
-  if (tid == 0) mbar_init(&s_never, 1);
-  // per-warp digit counters: counts while ranking, then each warp's offset inside the digit's
-  // run; they are zeroed again while the tile is written out
-  for (u32 i = tid; i < kSWarps * WSMAX; i += kSThreads) whist[i] = 0;
-  const u64 per = lane_tiles(ntiles, j.lanes);
-  bool inject = (j.inject & kInjectRange) && blockIdx.x == 0 && tid == 0;  // testing: fail one run check
-  bool inject_wait = (j.inject & kInjectWait) && blockIdx.x == 0;  // testing: one wait runs out
-  __syncthreads();
-
-  for (u64 ln = blockIdx.x; ln < j.lanes; ln += gridDim.x) {
-    const u64 t0 = ln * per, t1 = min(ntiles, t0 + per);
-    if (t0 >= t1) break;  // later lanes are empty too
-    u64 b = find_bin(bins, nb, t0);
-    u64 cur = ~0ull;
-    u64 run[kDigitsPerThread];    // this thread's digits: start of the next run, bin-relative
-    for (u64 t = t0; t < t1; t++) {
-      while (b + 1 < nb && bins[b + 1].tile_start <= t) b++;
-      const Bin* bp = &bins[b];
-      const u32 lo = bp->lo, W = bp->W, BW = bucket_bits(W, bp->flags), nd = 1u << BW;
-      const bool dom = (bp->flags & kBinDom) != 0;
-      Key<KW> K = {};
-      u32 dK = 0;
-      if (dom) {
-#pragma unroll
-        for (int q = 0; q < KW; q++) K.w[q] = bp->dom[q];
-        dK = digit_of<KW>(K, lo, W);
-      }
-      // bucket of a staged record (a digit window never reaches past the key, so only the
-      // comparisons with a dominant key need the key mask)
-      auto bucket = [&](const u64* rec) -> u32 {
-        if (!dom) return staged_digit<KW>(rec, lo, W);
-        Key<KW> k;
-#pragma unroll
-        for (int q = 0; q < KW; q++) k.w[q] = rec[q] & j.keymask[q];
-        return bucket_of<KW>(k, lo, W, true, K, dK);
-      };
-      // per-warp counters with a row stride of this bin's bucket count (every tile zeroes the
-      // rows it used, so the rows of a narrower or wider digit start at zero too)
-      const u32 WS = nd < 2 ? 2 : nd;
-      u16* wh = whist + warp * WS;
-      const u64 begin = bp->begin, size = bp->size;
-      const u64 tib = t - bp->tile_start;
-      const u32 parity = bp->parity;
-      if ((bp->flags & kBinEqual) || tib * T >= size) continue;  // finished bin (or inconsistent list)
-      const u64 r0 = tib * T;
-      const u32 cnt = (u32)min((u64)T, size - r0);
-      u64* dstb = j.buf[parity ^ 1];
-
-      // the tile comes in by bulk copies when it starts on a 16-byte boundary (an even word
-      // count per record: always), one per warp strip, each completing on its own barrier so
-      // that a warp starts ranking as soon as its strip has landed; else by 16- or 8-byte
-      // copies of every thread
-      const u64* src = j.buf[parity] + (begin + r0) * RW;
-      const u32 bytes = cnt * RW * 8;
-      const bool bulk = ((((uintptr_t)src) | bytes) & 15) == 0;
-      if (!bulk) {
-        load_words_async<kSThreads>(stage, src, (u64)cnt * RW);
-      } else if (lane == 0) {
-        // (strip boundaries are multiples of PW records: 16-byte aligned, as is the tile's end)
-        const u32 a = warp * PW, e = min(cnt, a + PW);
-        fence_proxy_async_smem();  // the last tile's reads of the stage are done (barrier)
-        if (e > a) bulk_load(stage + (u64)a * RW, src + (u64)a * RW, (e - a) * RW * 8, &s_bar[warp]);
-        else mbar_arrive(&s_bar[warp]);
-      }
-      // the lane's next tile of this bin comes into L2 while this one is processed
-      if (tid == 0 && t + 1 < t1 && r0 + T < size)
-        prefetch_l2(j.buf[parity] + (begin + r0 + T) * RW, min((u64)T, size - r0 - T) * RW * 8);
-      if (b != cur) {  // first tile of this lane's part of the bin: its run starts
-        cur = b;
-        const u64* sg = j.seg + ((ln + b) << j.wmax);
-        const u32 D = digits_per_thread(nd);
-#pragma unroll
-        for (u32 q = 0; q < kDigitsPerThread; q++) {
-          const u32 v = D * tid + q;
-          run[q] = (q < D && v < nd) ? sg[v] : 0;
-        }
-      }
-      // bounded: a strip that has not landed after j.wd_polls suspended waits is reported after
-      // the ranking (its warp ranks nothing; the copies cannot be cancelled, so the CTA waits
-      // for every strip once more, with the default limit, before it gives up); every thread
-      // takes the same way out
-      bool failed = false;
-      if (bulk) {
-        failed = !mbar_wait(inject_wait && warp == 0 ? &s_never : &s_bar[warp], inject_wait && warp == 0 ? 0u : bar_phase,
-                            j.wd_polls);
-        inject_wait = false;
-        failed = __any_sync(kFull, failed);  // (the whole warp skips its strip)
-      } else {
-        cp_async_wait_all();
-        __syncthreads();
-      }
-
-      // Stable rank of one item (one record per lane, lanes in record order) among the warp's
-      // records of its bucket: the count before this item (per-warp counter) + the lanes below
-      // it with the same bucket.  The lanes sharing a bucket are found without a vote per
-      // digit bit: every lane writes its id into its bucket's byte, and all lanes of a bucket
-      // read back the same winner.  With 2^9 buckets and 32 lanes most items have no shared
-      // bucket (every lane reads its own id back: one vote tells); otherwise lanes are grouped
-      // by their winner's id, which takes 5 votes.  Lanes without a record (valid = false)
-      // write nothing and form groups of their own.  Returns (rank | bucket << 16), or all ones.
-      u8* wn = winner + warp * WS;
-      auto rank_item = [&](u32 d, bool valid) -> u32 {
-        if (valid) wn[d] = (u8)lane;
-        __syncwarp();
-        const u32 w = valid ? (u32)wn[d] : (u32)lane, old = valid ? (u32)wh[d] : 0u;
-        u32 peers = 1u << lane;
-        if (__any_sync(kFull, w != (u32)lane)) {
-          u32 x = 0;
-#pragma unroll
-          for (int b = 0; b < 5; b++) {
-            const u32 v = __ballot_sync(kFull, (w >> b) & 1u);
-            x |= v ^ (0u - ((w >> b) & 1u));
-          }
-          peers = ~x;
-        }
-        const u32 before = __popc(peers & ltmask);
-        __syncwarp();  // (every lane has read the bucket's byte and counter)
-        if (valid && before == 0) wh[d] = (u16)(old + __popc(peers));
-        return valid ? ((old + before) | (d << 16)) : 0xffffffffu;
-      };
-      // stable rank: warp w owns records [w*PW, (w+1)*PW), visited in order
-      u32 packed[IT];
-      if (failed) {
-#pragma unroll
-        for (int it = 0; it < IT; it++) packed[it] = 0xffffffffu;
-      } else if (cnt == T) {
-        // first every item's bucket, then the ranks
-        u32 dg[IT];
-        if (!dom) {  // (the two loops differ in the bucket function only)
-#pragma unroll
-          for (int it = 0; it < IT; it++) dg[it] = staged_digit<KW>(stage + (u64)(warp * PW + it * 32 + lane) * RW, lo, W);
-        } else {
-#pragma unroll
-          for (int it = 0; it < IT; it++) dg[it] = bucket(stage + (u64)(warp * PW + it * 32 + lane) * RW);
-        }
-#pragma unroll
-        for (int it = 0; it < IT; it++) packed[it] = rank_item(dg[it], true);
-      } else {
-#pragma unroll
-        for (int it = 0; it < IT; it++) {
-          const u32 r = warp * PW + it * 32 + lane;
-          const bool valid = r < cnt;
-          packed[it] = rank_item(valid ? bucket(stage + (u64)r * RW) : 0u, valid);
-        }
-      }
-      if (__syncthreads_or(failed)) {
-        if (tid == 0) report(ctl, kErrTimeout);
-        if (lane == 0) mbar_wait(&s_bar[warp], bar_phase, kWaitPolls);
-        __syncwarp();
-        return;
-      }
-      if (bulk) bar_phase ^= 1;
-      // Thread tid owns digits [D*tid, D*tid + D): it turns their per-warp counts into each
-      // warp's offset inside the digit's run (two 16-bit counters per 32-bit access), then one
-      // block scan of the threads' totals gives the digits' first slots in the tile.
-      const u32 D = digits_per_thread(nd);
-      const u32 v0 = D * tid;
-      u32 c[kDigitsPerThread];
-#pragma unroll
-      for (u32 q = 0; q < kDigitsPerThread; q++) c[q] = 0;
-      if (v0 < nd) {
-        u32* wh32 = (u32*)whist;
-#pragma unroll
-        for (u32 p2 = 0; p2 < kDigitsPerThread / 2; p2++) {
-          if (2 * p2 >= D) break;
-          u32 a0 = 0, a1 = 0;
-#pragma unroll
-          for (int w = 0; w < kSWarps; w++) {
-            u32* x = wh32 + w * (WS >> 1) + (v0 >> 1) + p2;
-            const u32 y = *x;
-            *x = a0 | (a1 << 16);
-            a0 += y & 0xffffu;
-            a1 += y >> 16;
-          }
-          c[2 * p2] = a0;
-          c[2 * p2 + 1] = a1;
-        }
-      }
-      u32 mine = 0;
-#pragma unroll
-      for (u32 q = 0; q < kDigitsPerThread; q++) mine += c[q];
-      u32 tb = block_exclusive_sum<kSThreads>(mine, scan_scr);
-      // destinations of this thread's runs; a run that would leave its bin (possible only with
-      // corrupted counts) is reported and not written
-#pragma unroll
-      for (u32 q = 0; q < kDigitsPerThread; q++) {
-        const u32 v = v0 + q;
-        if (q >= D || v >= nd) break;
-        const u32 cq = c[q];
-        const u64 first = run[q];
-        run[q] += cq;
-        u64 g = begin + first - tb;
-        bool bad = cq && (first > size || cq > size - first);
-        if (cq && inject) {
-          bad = true;
-          inject = false;
-        }
-        if (bad) {
-          report(ctl, kErrInternal);
-          g = kSkip;
-        }
-        tbase[v] = tb;
-        gbase[v] = g;
-        tb += cq;
-      }
-      __syncthreads();
-      if (cnt == T) {
-#pragma unroll
-        for (int it = 0; it < IT; it++) {
-          const u32 d = packed[it] >> 16;
-          const u32 slot = tbase[d] + wh[d] + (packed[it] & 0xffffu);
-          slotw[slot] = (warp * PW + it * 32 + lane) | (d << 16);
-        }
-      } else {
-#pragma unroll
-        for (int it = 0; it < IT; it++) {
-          if (packed[it] != 0xffffffffu) {
-            const u32 d = packed[it] >> 16;
-            const u32 slot = tbase[d] + wh[d] + (packed[it] & 0xffffu);
-            slotw[slot] = (warp * PW + it * 32 + lane) | (d << 16);
-          }
-        }
-      }
-      __syncthreads();
-      // per-warp counters back to zero for the next tile (nothing reads them before then)
-      for (u32 v = tid; v < nd; v += kSThreads) {
-#pragma unroll
-        for (int w = 0; w < kSWarps; w++) whist[w * WS + v] = 0;
-      }
-      // write the tile in digit order: consecutive slots of one digit go to consecutive records
-      if (RW == 2) {
-        for (u32 s = tid; s < cnt; s += kSThreads) {
-          const u32 sw = slotw[s];
-          const u64 g = gbase[sw >> 16];
-          const ulonglong2 v = *reinterpret_cast<const ulonglong2*>(stage + 2 * (sw & 0xffffu));
-          if (g == kSkip) continue;
-          __stcs(reinterpret_cast<ulonglong2*>(dstb + 2 * (g + s)), v);
-        }
-      } else {
-        // whole warps write consecutive slots: lane k * P + piece moves one piece (16 bytes if
-        // RW is even, else 8) of slot s0 + k, so a store instruction covers whole records of a run
-        // (P <= 32: records are at most 256 bytes)
-        const bool pairs = (RW & 1) == 0;
-        const u32 P = pairs ? RW >> 1 : RW, rpw = 32 / P;
-        const u32 k = lane / P, piece = lane - k * P;
-        for (u32 s0 = warp * rpw; s0 < cnt; s0 += kSWarps * rpw) {
-          const u32 s = s0 + k;
-          if (k >= rpw || s >= cnt) continue;
-          const u32 sw = slotw[s];
-          const u64 g = gbase[sw >> 16];
-          if (g == kSkip) continue;
-          const u64* sp = stage + (u64)(sw & 0xffffu) * RW;
-          u64* d = dstb + (g + s) * RW;
-          if (pairs)
-            __stcs(reinterpret_cast<ulonglong2*>(d) + piece, reinterpret_cast<const ulonglong2*>(sp)[piece]);
-          else
-            __stcs(d + piece, sp[piece]);
-        }
-      }
-      __syncthreads();
-    }
-  }
 }
 
 // -------------------------------------------------------------------- classify
@@ -1115,57 +762,6 @@ __global__ void k_read_counts(Job j, u64* out, u32 nd) {
 }
 
 // ------------------------------------------------------------------- launchers
-size_t scatter_smem_bytes(const Job& j) { return scatter_layout(j.T, j.RW, j.wmax).total; }
-
-// Largest shared memory either level kernel needs for tiles of T records.
-size_t level_smem_for(u32 T, u32 RW, u32 KW, u32 wmax) {
-  const size_t a = scatter_layout(T, RW, wmax).total, b = hist_smem_bytes_for(T, KW);
-  return a > b ? a : b;
-}
-
-template <int KW, int RWT, int IT>
-static cudaError_t launch_scatter_t(const Job& j, int level, u32 grid, cudaStream_t s, int* occ) {
-  const size_t sm = scatter_smem_bytes(j);
-  cudaFuncSetAttribute(k_scatter<KW, RWT, IT>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
-  if (occ) {
-    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(occ, k_scatter<KW, RWT, IT>, kSThreads, sm) != cudaSuccess ||
-        *occ < 1)
-      *occ = 1;
-    return cudaSuccess;
-  }
-  k_scatter<KW, RWT, IT><<<grid, kSThreads, sm, s>>>(j, level);
-  return cudaGetLastError();
-}
-
-template <int KW, int IT>
-static cudaError_t scatter_rw(const Job& j, int level, u32 grid, cudaStream_t s, int* occ) {
-  switch (j.RW) {
-    case 1: return launch_scatter_t<KW, 1, IT>(j, level, grid, s, occ);
-    case 2: return launch_scatter_t<KW, 2, IT>(j, level, grid, s, occ);
-    case 3: return launch_scatter_t<KW, 3, IT>(j, level, grid, s, occ);
-    case 4: return launch_scatter_t<KW, 4, IT>(j, level, grid, s, occ);
-    default: return launch_scatter_t<KW, 0, IT>(j, level, grid, s, occ);
-  }
-}
-
-template <int KW>
-static cudaError_t scatter_it(const Job& j, int level, u32 grid, cudaStream_t s, int* occ) {
-  switch (j.T / kSThreads) {
-    case 16: return scatter_rw<KW, 16>(j, level, grid, s, occ);
-    case 8: return scatter_rw<KW, 8>(j, level, grid, s, occ);
-    case 4: return scatter_rw<KW, 4>(j, level, grid, s, occ);
-    case 2: return scatter_rw<KW, 2>(j, level, grid, s, occ);
-    default: return scatter_rw<KW, 1>(j, level, grid, s, occ);
-  }
-}
-
-int scatter_ctas_per_sm(const Job& j) {
-  int n = 1;
-  if (j.KW == 1) scatter_it<1>(j, 0, 0, 0, &n);
-  else scatter_it<2>(j, 0, 0, 0, &n);
-  return n;
-}
-
 static size_t hist_smem(const Job& j) { return hist_smem_bytes_for(j.T, j.KW); }
 
 int hist_ctas_per_sm(const Job& j) {
@@ -1213,11 +809,6 @@ int launch_hist(const Job& j, int level, int mode, cudaStream_t s) {
     k_hist<2><<<grid, kThreads, sm, s>>>(j, level, mode);
   }
   return cudaGetLastError() == cudaSuccess ? 1 : -1;
-}
-
-int launch_scatter(const Job& j, int level, u32 grid, cudaStream_t s) {
-  cudaError_t e = j.KW == 1 ? scatter_it<1>(j, level, grid, s, nullptr) : scatter_it<2>(j, level, grid, s, nullptr);
-  return e == cudaSuccess ? 1 : -1;
 }
 
 int classify_ctas_per_sm() { return kClsCtas; }

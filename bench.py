@@ -198,6 +198,35 @@ def replica_throughput(n: int, world: int, steps: int, max_ms: float) -> float:
     return n * world * steps / (max_ms / 1e3)
 
 
+def host_cpu():
+    """The host's CPU model and logical core count (for the CPU baseline's record)."""
+    model = None
+    try:  # lscpu names Arm cores too ("Neoverse-V2"), where /proc/cpuinfo gives part numbers
+        out = subprocess.run(["lscpu"], capture_output=True, text=True, timeout=10).stdout
+        for line in out.splitlines():
+            if line.lower().startswith("model name:"):
+                model = line.split(":", 1)[1].strip()
+                break
+    except (OSError, subprocess.SubprocessError):
+        pass
+    try:
+        if model:
+            raise OSError
+        with open("/proc/cpuinfo") as f:
+            for line in f:
+                key = line.split(":")[0].strip().lower()
+                if key in ("model name", "cpu part", "hardware") and ":" in line:
+                    model = line.split(":", 1)[1].strip()
+                    if key == "model name":
+                        break
+    except OSError:
+        pass
+    if not model:
+        import platform
+        model = platform.processor() or platform.machine()
+    return {"cpu_model": model, "nproc": os.cpu_count()}
+
+
 def cpu_baseline(kind, n_full, R, K, seed, budget_s):
     """The oracle (single-threaded LSD radix sort) on a bounded sample of the workload."""
     import oracle
@@ -212,7 +241,8 @@ def cpu_baseline(kind, n_full, R, K, seed, budget_s):
     oracle.sort(a, K)
     dt = time.perf_counter() - t0
     return {"value": n_s / dt, "unit": "records/s", "cores": 1, "kind": "oracle",
-            "sample": f"first {n_s} records of the same workload, one single-threaded sort ({dt:.1f} s)"}
+            "sample": f"first {n_s} records of the same workload, one single-threaded sort ({dt:.1f} s)",
+            **host_cpu()}
 
 
 def reference_arm(args):
@@ -241,7 +271,7 @@ def reference_arm(args):
         "scaling": "weak", "vs_baseline": None, "dtype": "u64", "data": "synthetic",
         "config": {"workload": args.workload, "n": n_full, "rec_size": R, "key_size": K, "keys": desc},
         "cpu_baseline": {"value": v, "unit": "records/s", "cores": 1, "kind": "oracle",
-                         "sample": f"first {n_s} records of the workload per step"},
+                         "sample": f"first {n_s} records of the workload per step", **host_cpu()},
         "e2e": {"value": v, "unit": "records/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
     }
     print(json.dumps(line), flush=True)
@@ -727,12 +757,25 @@ def main():
     def one_sort():
         rg.sort(buf, K, tmp=tmp, stream=stream)
 
-    for _ in range(args.warmup):
-        buf.copy_(pristine)
-        one_sort()
-    torch.cuda.synchronize()
+    # the warm-up steps time every kernel (the per-kernel split and which kernel dominates);
+    # the timed steps then bracket only the dominant kernel with events, so that the events
+    # disturb the timed sort as little as possible
+    with rg.profile() as warm_prof:
+        for _ in range(args.warmup):
+            buf.copy_(pristine)
+            one_sort()
+        torch.cuda.synchronize()
     if rg.status() != 0:
         raise SystemExit("device status error during warm-up")
+    per = {}
+    for name, level, ms in warm_prof.records:
+        e = per.setdefault(name, {"launches": 0, "ms": 0.0})
+        e["launches"] += 1
+        e["ms"] += ms
+    all_ms = sum(e["ms"] for e in per.values()) or 1.0
+    for e in per.values():
+        e["share"] = e["ms"] / all_ms
+    dominant = max(per, key=lambda k: per[k]["ms"])
 
     ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(args.steps)]
     gpu_id = local
@@ -740,7 +783,7 @@ def main():
     if dist:
         dist.barrier()
     torch.cuda.synchronize()
-    with ClockSampler(gpu_id) as clk, rg.profile() as prof:
+    with ClockSampler(gpu_id) as clk, rg.profile(kernels=[dominant]) as prof:
         for a, b in ev:
             buf.copy_(pristine)  # restore the unsorted input (untimed)
             a.record(stream)
@@ -757,37 +800,30 @@ def main():
     tot_ms = max_over_ranks(sum(step_ms), dist, dev)
     value = replica_throughput(n, world, args.steps, tot_ms)
 
-    # per-kernel shares and the dominant kernel's roofline (CUDA events on the launch stream)
-    per = {}
-    for name, level, ms in prof.records:
-        e = per.setdefault(name, {"launches": 0, "ms": 0.0})
-        e["launches"] += 1
-        e["ms"] += ms
-    all_ms = sum(e["ms"] for e in per.values()) or 1.0
-    for e in per.values():
-        e["share"] = e["ms"] / all_ms
-    dominant = max(per, key=lambda k: per[k]["ms"])
-    units = {"scatter": (0, 2 * n * R), "hist": (0, n * R), "chunk": (None, 2 * n * R)}
+    # the dominant kernel's roofline (CUDA events on the launch stream, timed steps)
+    # bytes of one working launch (launches of empty levels, which return at once, are left out)
+    units = {"scatter": 2 * n * R, "hist": n * R, "chunk": 2 * n * R}
     peak, peak_src = measured_peaks()
     roof = None
     if dominant in units:
-        lvl, bytes_per_launch = units[dominant]
-        ms = [m for (nm, lv, m) in prof.records if nm == dominant and (lvl is None or lv == lvl)]
+        bytes_per_launch = units[dominant]
+        all_ms = [m for (nm, lv, m) in prof.records if nm == dominant]
+        ms = [m for m in all_ms if m > 0.05 * max(all_ms)]
         avg = statistics.mean(ms)
         achieved = bytes_per_launch / (avg / 1e3) / 1e9
         roof = {"bound": "hbm", "kernel": dominant, "achieved": achieved, "peak": peak, "unit": "GB/s",
                 "frac": achieved / peak, "peak_source": f"{peak_src} hbm_gbs (MEASURED_PEAKS.json)",
                 "traffic": committed_traffic(dominant, args.workload), "avg_launch_ms": avg,
                 "bytes_per_launch": bytes_per_launch,
-                "launches_used": len(ms)}
+                "launches_used": len(ms), "launches_note": "every working launch of the timed steps (all levels)"}
     if args.profile_out:
         with open(args.profile_out, "w") as f:
-            json.dump({"records": prof.records, "per_kernel": per}, f, indent=1)
+            json.dump({"records": warm_prof.records, "per_kernel": per, "timed_dominant": prof.records}, f, indent=1)
 
     # algorithmic bytes of the whole sort for uniform keys: read once for the level-0
     # histogram, read+write per distribution level, read+write for the on-chip pass
-    levels = sorted({lv for (nm, lv, m) in prof.records if nm == "scatter" and m > 0.05 * statistics.mean(
-        [x for (q, _, x) in prof.records if q == "scatter"] or [1])})
+    levels = sorted({lv for (nm, lv, m) in warm_prof.records if nm == "scatter" and m > 0.05 * statistics.mean(
+        [x for (q, _, x) in warm_prof.records if q == "scatter"] or [1])})
     b_alg = n * R * (1 + 2 * len(levels) + 2)
     ms_step = tot_ms / args.steps
     hbm = {"b_alg_bytes": b_alg, "levels": len(levels), "gbs": b_alg / (ms_step / 1e3) / 1e9}
@@ -821,7 +857,10 @@ def main():
             "config": {"workload": args.workload, "n": n, "rec_size": R, "key_size": K, "keys": desc,
                        "seed": seed, "parallelism": f"replicas{world}", "plan": rg.get_plan(),
                        "l2": "input 16 GB >> L2; pristine input restored into the sort buffer before every step"},
-            "roofline": roof, "hbm": hbm, "kernels": per, "gpu_launches": launches, "clocks": clk.summary(),
+            "roofline": roof, "hbm": hbm, "kernels": per,
+            "kernels_note": "per-kernel split from the warm-up steps (every launch timed); the timed steps "
+                            "bracket only the dominant kernel with events",
+            "gpu_launches": launches, "clocks": clk.summary(),
             "e2e": e2e, "cpu_baseline": cpu, "step_ms": step_ms,
         }
         print(json.dumps(line), flush=True)

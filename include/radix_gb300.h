@@ -230,6 +230,13 @@ rs_status radix_sort_profile(int enable);
 int64_t radix_sort_profile_read(rs_kernel_time *out, int64_t max);
 
 /*
+ * Which kernels radix_sort_profile brackets with events: bit k set = kernel id k (RS_K_*) is
+ * timed (default: all).  Fewer events disturb the timed work less: a benchmark can time the
+ * whole call and one kernel together.  Applies to launches made after the call.
+ */
+rs_status radix_sort_profile_kernels(uint32_t mask);
+
+/*
  * radix_sort without any allocation.  (No counterpart in the paper: this is an interface
  * for callers that cannot allocate.)
  *
@@ -254,8 +261,8 @@ int64_t radix_sort_profile_read(rs_kernel_time *out, int64_t max);
  * Limits:
  *   The workspace needed for (n, rec_size, key_size) must fit the 64 MiB array, else the
  *   call returns RS_ERR_TOO_LARGE and launches nothing.  With the default plan that is about
- *   3.5 x 10^7 records of 16 bytes (8-byte keys), 3.7 x 10^7 of 8 bytes, 2.5 x 10^7 of
- *   24 bytes (16-byte keys).
+ *   3.0 x 10^7 records of 8 or 16 bytes (8-byte keys), 2.4 x 10^7 of 24 bytes (16-byte
+ *   keys); radix_sort_workspace_bytes tells for any shape.
  * Sharing:
  *   Every call uses the same array, on every stream.  Calls whose work overlaps on the GPU
  *   (on different streams, or from different host threads without ordering) race on it and

@@ -203,9 +203,15 @@ class profile:
     """Context manager: per-kernel CUDA-event timings of the library's launches.
 
     ``with profile() as p: ...`` then ``p.records`` = [(kernel_name, level, ms), ...].
+    ``kernels``: names (``KERNEL_NAMES`` values) to time; default all.
     """
 
+    def __init__(self, kernels=None):
+        ids = {v: k for k, v in KERNEL_NAMES.items()}
+        self.mask = 0xFFFFFFFF if kernels is None else sum(1 << ids[k] for k in kernels)
+
     def __enter__(self):
+        check(lib().radix_sort_profile_kernels(self.mask), "radix_sort_profile_kernels")
         check(lib().radix_sort_profile(1), "radix_sort_profile")
         self.records = []
         return self
@@ -213,6 +219,7 @@ class profile:
     def __exit__(self, *exc):
         L = lib()
         L.radix_sort_profile(0)
+        L.radix_sort_profile_kernels(0xFFFFFFFF)
         n = L.radix_sort_profile_read(None, 0)
         buf = (RsKernelTime * max(1, n))()
         got = L.radix_sort_profile_read(buf, n)

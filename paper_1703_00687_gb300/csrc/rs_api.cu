@@ -261,6 +261,7 @@ struct ProfRec {
 };
 static std::mutex g_prof_mu;
 static bool g_prof_on = false;
+static uint32_t g_prof_mask = ~0u;  // kernels (bit RS_K_*) that get events while profiling
 static std::vector<ProfRec> g_prof;     // records of this profiling session
 static std::vector<cudaEvent_t> g_evpool;
 static size_t g_evnext = 0;
@@ -280,7 +281,7 @@ static int timed(u32 kernel, u32 level, cudaStream_t s, F&& launch) {
   bool on;
   {
     std::lock_guard<std::mutex> lk(g_prof_mu);
-    on = g_prof_on;
+    on = g_prof_on && ((g_prof_mask >> kernel) & 1u);
     if (on) {
       r.a = prof_event();
       r.b = prof_event();
@@ -712,6 +713,12 @@ rs_status radix_sort_profile(int enable) {
     g_evnext = 0;
   }
   g_prof_on = enable != 0;
+  return RS_OK;
+}
+
+rs_status radix_sort_profile_kernels(uint32_t mask) {
+  std::lock_guard<std::mutex> lk(g_prof_mu);
+  g_prof_mask = mask;
   return RS_OK;
 }
 

@@ -33,7 +33,7 @@ constexpr int kCWarps = kCThreads / 32;
 constexpr int kEsMax = 48;       // largest bucket finished by enumeration sort
 constexpr int kWinBits = 12;     // digit of the on-chip distribution pass
 constexpr int kIdxBits = 13;     // input positions of a chunk (chunk_max <= 2^13)
-constexpr int kChunkItems = 9;   // positions per thread (chunk_max <= kCThreads * this)
+constexpr int kChunkItems = 8;   // positions per thread (chunk_max <= kCThreads * this)
 constexpr int kCntWords = 1 << (kWinBits - 1);  // counters of a distribution, two 16-bit per word
 // dynamic shared memory of the chunk CTA (two CTAs and their static shared memory fit an SM)
 constexpr size_t kChunkSmem = 111 * 1024;
@@ -462,7 +462,6 @@ __global__ void __launch_bounds__(kCThreads, kChunkCtas) k_chunk(Job j) {
   __shared__ __align__(8) u64 s_bar[kCWarps];  // bar w: warp w's strip of the chunk has landed
   const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
   constexpr u32 kIdxMask = (1u << kIdxBits) - 1u;
-  constexpr u32 kStrip = kChunkItems * 32;  // records of a warp strip (kCWarps strips cover chunk_max)
   u32 bar_phase = 0;
 
   // thread 0: publish ticket t with its descriptor `raw` (an unusable one is reported, not
@@ -506,16 +505,19 @@ __global__ void __launch_bounds__(kCThreads, kChunkCtas) k_chunk(Job j) {
     const u32 sz = ch.size;
     const bool in_place = !(ch.flags & kChSrcTmp), copy_only = (ch.flags & kChCopyOnly) != 0;
     // the records come in by bulk copies when they start on a 16-byte boundary (an even word
-    // count per record: always), one per warp strip of kStrip records, each completing on its
+    // count per record: always), one per warp strip of S records, each completing on its
     // own barrier; else by 16- or 8-byte copies of every thread
     const u64* src = j.buf[in_place ? 0 : 1] + ch.begin * RW;
     const u32 bytes = sz * RW * 8;
     const bool load = sz && !(copy_only && in_place);
     const bool bulk = load && ((((uintptr_t)src) | bytes) & 15) == 0;
+    // strips of S records, a multiple of 32: the warps share the chunk evenly, S <= 32 *
+    // kChunkItems (kCWarps * 32 * kChunkItems >= chunk_max)
+    const u32 S = 32u * ((sz + kCThreads - 1) / kCThreads);
     if (load && !bulk) load_words_async<kCThreads>(stage, src, (u64)sz * RW);
     if (bulk && lane == 0) {
-      // (strip boundaries are multiples of kStrip records: 16-byte aligned, as is the chunk's end)
-      const u32 a = warp * kStrip, e = min(sz, a + kStrip);
+      // (strip boundaries are multiples of 32 records: 16-byte aligned, as is the chunk's end)
+      const u32 a = min(sz, warp * S), e = min(sz, a + S);
       fence_proxy_async_smem();  // the last chunk's reads of the stage are done (barrier)
       if (e > a) bulk_load(stage + (u64)a * RW, src + (u64)a * RW, (e - a) * RW * 8, &s_bar[warp]);
       else mbar_arrive(&s_bar[warp]);
@@ -581,10 +583,10 @@ __global__ void __launch_bounds__(kCThreads, kChunkCtas) k_chunk(Job j) {
       u32 held[kChunkItems];  // (digit << 16) | rank among the digit's records counted before
 #pragma unroll
       for (int k = 0; k < kChunkItems; k++) {
-        const u32 i = warp * kStrip + k * 32 + lane;  // (this warp's strip)
+        const u32 i = warp * S + k * 32 + lane;  // (this warp's strip)
         held[k] = 0xffffffffu;
         ck[k] = 0;
-        if (i < sz) {
+        if (i < sz && k * 32 < S) {
           ck[k] = (cs.keypart<KW>(c.key(i)) << kIdxBits) | i;
           const u32 d = (u32)(ck[k] >> cs.dshift) & cs.dmask;
           const u32 old = atomicAdd(&c.cnt[d >> 1], 1u << ((d & 1) * 16));
@@ -661,7 +663,7 @@ __global__ void __launch_bounds__(kCThreads, kChunkCtas) k_chunk(Job j) {
 #pragma unroll
         for (int k = 0; k < kChunkItems; k++)
           if (held[k] != 0xffffffffu)
-            c.out[c.count_of(held[k] >> 16) + (held[k] & 0xffffu)] = (u16)(warp * kStrip + k * 32 + lane);
+            c.out[c.count_of(held[k] >> 16) + (held[k] & 0xffffu)] = (u16)(warp * S + k * 32 + lane);
         __syncthreads();
         finish_round(c, 0, sz, dig, &s_top);
         while (s_top) {  // s_top is final after the barrier that ends every round

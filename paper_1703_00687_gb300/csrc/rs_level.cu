@@ -109,7 +109,6 @@ __global__ void __launch_bounds__(kThreads) k_init_plain(Job j, u32 lo, u32 W) {
     b.W = W;
     j.bins[0][0] = b;
   }
-  for (u32 v = threadIdx.x; v < nd; v += kThreads) j.base[0][v] = 0;
 }
 
 __global__ void k_init_single_chunk(Job j) {
@@ -196,7 +195,6 @@ __global__ void __launch_bounds__(kThreads) k_init_segments(Job j) {
     bn.lo = lo;
     bn.W = W;
     j.bins[0][idx] = bn;
-    for (u32 v = 0; v < nd; v++) j.base[0][bo + v] = 0;
   }
 }
 
@@ -248,24 +246,10 @@ __device__ void finish_bin(const Job& j, int L, u64 b, int mode) {
     }
   }
   __syncthreads();
-  if (s_ret) {
-    if (s_ret == 2)
-      for (u32 v = threadIdx.x; v < nd; v += kThreads) base[v] = 0;
-    return;
-  }
-  if (mode == 2) return;
-  // nd <= 1024: two entries per thread
-  const u32 v0 = 2 * threadIdx.x;
-  const u64 c0 = v0 < nd ? __ldcg(base + v0) : 0;
-  const u64 c1 = v0 + 1 < nd ? __ldcg(base + v0 + 1) : 0;
-  u64 tot;
-  const u64 ex = block_scan_value64(c0 + c1, scr, &tot);
-  if (v0 < nd) base[v0] = ex;
-  if (v0 + 1 < nd) base[v0 + 1] = ex + c0;
-  if (mode == 1 && threadIdx.x == 0) bp->flags &= ~kBinRedo;
-  // Run starts of the scatter: the part of the bin inside lane c writes digit v from
-  // bucket base + (records of digit v in the bin's earlier lanes).  Every lane that holds
-  // tiles of the bin has stored its counts in its segment before the bin was finished.
+  if (s_ret) return;
+  // Every lane that holds tiles of the bin (lanes cfirst..clast: its tiles are consecutive) has
+  // stored its digit counts in its segment; their sums are the bucket counts.  nd <= 1024:
+  // two entries per thread.
   const u64 per = lane_tiles(j.ctl->ntiles[L], j.lanes);
   const u64 ts = bp->tile_start, nt = ceil_div(size, (u64)j.T);
   const u64 cfirst = ts / per, clast = (ts + nt - 1) / per;
@@ -273,6 +257,25 @@ __device__ void finish_bin(const Job& j, int L, u64 b, int mode) {
     if (threadIdx.x == 0) report(j.ctl, kErrOverflow);
     return;
   }
+  const u32 v0 = 2 * threadIdx.x;
+  u64 c0 = 0, c1 = 0;
+  for (u64 c = cfirst; c <= clast; c++) {
+    const u64* sg = j.seg + ((c + b) << j.wmax);
+    if (v0 < nd) c0 += __ldcg(sg + v0);
+    if (v0 + 1 < nd) c1 += __ldcg(sg + v0 + 1);
+  }
+  if (mode == 2) {  // the counts themselves
+    if (v0 < nd) base[v0] = c0;
+    if (v0 + 1 < nd) base[v0 + 1] = c1;
+    return;
+  }
+  u64 tot;
+  const u64 ex = block_scan_value64(c0 + c1, scr, &tot);
+  if (v0 < nd) base[v0] = ex;
+  if (v0 + 1 < nd) base[v0 + 1] = ex + c0;
+  if (mode == 1 && threadIdx.x == 0) bp->flags &= ~kBinRedo;
+  // Run starts of the scatter: the part of the bin inside lane c writes digit v from
+  // bucket base + (records of digit v in the bin's earlier lanes).
   u64 r0 = ex, r1 = ex + c0;
   for (u64 c = cfirst; c <= clast; c++) {
     u64* sg = j.seg + ((c + b) << j.wmax);
@@ -323,7 +326,6 @@ __global__ void __launch_bounds__(kThreads, 2) k_hist(Job j, int level, int mode
     __syncthreads();
     const Bin* bb = &bins[b];
     const u32 nd = 1u << bucket_bits(bb->W, bb->flags);
-    const u64 bo = bb->base_off;
     const u64 sid = lane_id + b;  // segment of (lane, bin)
     if (sid >= j.cap_seg) {    // cannot happen: lanes + bins segments are allocated
       if (tid == 0) report(ctl, kErrOverflow);
@@ -337,8 +339,7 @@ __global__ void __launch_bounds__(kThreads, 2) k_hist(Job j, int level, int mode
         h += hist[(c << kWMax) + v];
         hist[(c << kWMax) + v] = 0;
       }
-      if (h) atomicAdd(&j.base[L][bo + v], (u64)h);
-      if (mode != 2) sg[v] = h;  // this lane's part of the bin (the scatter's run starts)
+      sg[v] = h;  // this lane's counts of the bin (summed when the bin is finished)
     }
     if (want_masks) {
 #pragma unroll
@@ -578,6 +579,70 @@ __global__ void __launch_bounds__(kClsThreads, kClsCtas) k_classify(Job j, int l
   __shared__ int s_last;
   const int tid = threadIdx.x, lane = tid & 31;
   const u32 cm = j.chunk_max;
+  // Large sub-bins (the next level's bins) first, spread over every warp of the grid: unit u
+  // is bin u / 32 and its group u % 32 of 32 sub-bins, one per lane, so that the samples
+  // (random reads) of a bin with many large sub-bins are taken by many warps at once.
+  {
+    const u64 nw = (u64)gridDim.x * (kClsThreads / 32);
+    for (u64 u = (u64)blockIdx.x * (kClsThreads / 32) + (tid >> 5); u < nb * 32; u += nw) {
+      const Bin& bin = bins[u >> 5];
+      const u32 flags = bin.flags, W = bin.W;
+      const u32 nd = 1u << bucket_bits(W, flags), v = (u32)(u & 31) * 32 + lane;
+      if ((flags & kBinEqual) || v >= nd) continue;
+      const u64 size = bin.size;
+      const u64* bbase = j.base[L] + bin.base_off;
+      const u64 bv = bbase[v], next = v + 1 < nd ? bbase[v + 1] : size;
+      if (next < bv || next > size || next - bv <= cm) continue;  // (inconsistent bases: reported below)
+      u32 vdom = nd;  // a dominated bin's own key bucket is finished in the packing loop
+      if (flags & kBinDom) {
+        Key<KW> K;
+#pragma unroll
+        for (int q = 0; q < KW; q++) K.w[q] = bin.dom[q];
+        vdom = digit_of<KW>(K, bin.lo, W) + 1;
+      }
+      if (v == vdom) continue;
+      const u64 c = next - bv, rb = bin.begin + bv;
+      const u32 p1 = bin.parity ^ 1, blo = bin.lo;
+      // every key bit >= bin.lo is shared by the sub-bin; guess where its next digit starts
+      // from a sample, and whether one key holds most of it
+      Key<KW> K2;
+      u32 ndom;
+      u32 p = sample_sub_bin<KW>(j, j.buf[p1] + rb * j.RW, c, &K2, &ndom);
+      if (p == 0 || p > blo) p = blo;
+      if (p == 0) p = 1;
+      u32 nlo, nW;
+      plan_digit(c, p, cm, j.wmax, &nlo, &nW);
+      // a dominated bin takes one digit bit less, so its 2^(W+1) buckets need no more room
+      // than a plain bin's (the other keys are at most half of it)
+      const bool dom2 = ndom >= kDomSamples && nW >= 2;
+      if (dom2) {
+        nW -= 1;
+        nlo += 1;
+      }
+      const u32 nnd = 1u << bucket_bits(nW, dom2 ? kBinDom : 0u);
+      const u64 idx = atomicAdd(&ctl->nbins[N], 1ull);
+      const u64 bo = atomicAdd(&ctl->base_used[N], (u64)nnd);
+      if (idx >= j.cap_bins || bo + nnd > j.cap_base) {
+        report(ctl, kErrOverflow);
+        continue;
+      }
+      Bin nbn = {};
+      nbn.begin = rb;
+      nbn.size = c;
+      nbn.base_off = bo;
+      nbn.kand[0] = nbn.kand[1] = ~0ull;
+      nbn.lo = nlo;
+      nbn.W = nW;
+      nbn.parity = p1;
+      if (dom2) {
+        nbn.flags = kBinDom;
+#pragma unroll
+        for (int q = 0; q < KW; q++) nbn.dom[q] = K2.w[q];
+      }
+      j.bins[N][idx] = nbn;
+    }
+  }
+  // Then, per bin, the small sub-bins: finished records and chunk packing.
   for (u64 b = blockIdx.x; b < nb; b += gridDim.x) {
     const Bin bin = bins[b];
     if (bin.flags & kBinEqual) {  // finished without moving; copy back if it lives in tmp
@@ -613,47 +678,6 @@ __global__ void __launch_bounds__(kClsThreads, kClsCtas) k_classify(Job j, int l
           k = 0;          // chunk may reach across it
           S[v] = c ? cm + 1 : 0;
           if (c && p1) push_pieces(j, bin.begin + bv, c);
-        }
-        if (k == 3) {
-          const u64 rb = bin.begin + bv;
-          // every key bit >= bin.lo is shared by the sub-bin; guess where its next digit
-          // starts from a sample, and whether one key holds most of it
-          Key<KW> K2;
-          u32 ndom;
-          u32 p = sample_sub_bin<KW>(j, j.buf[p1] + rb * j.RW, c, &K2, &ndom);
-          if (p == 0 || p > bin.lo) p = bin.lo;
-          if (p == 0) p = 1;
-          u32 nlo, nW;
-          plan_digit(c, p, cm, j.wmax, &nlo, &nW);
-          // a dominated bin takes one digit bit less, so its 2^(W+1) buckets need no more room
-          // than a plain bin's (the other keys are at most half of it)
-          const bool dom2 = ndom >= kDomSamples && nW >= 2;
-          if (dom2) {
-            nW -= 1;
-            nlo += 1;
-          }
-          const u32 nnd = 1u << bucket_bits(nW, dom2 ? kBinDom : 0u);
-          const u64 idx = atomicAdd(&ctl->nbins[N], 1ull);
-          const u64 bo = atomicAdd(&ctl->base_used[N], (u64)nnd);
-          if (idx >= j.cap_bins || bo + nnd > j.cap_base) {
-            report(ctl, kErrOverflow);
-          } else {
-            Bin nbn = {};
-            nbn.begin = rb;
-            nbn.size = c;
-            nbn.base_off = bo;
-            nbn.kand[0] = nbn.kand[1] = ~0ull;
-            nbn.lo = nlo;
-            nbn.W = nW;
-            nbn.parity = p1;
-            if (dom2) {
-              nbn.flags = kBinDom;
-#pragma unroll
-              for (int q = 0; q < KW; q++) nbn.dom[q] = K2.w[q];
-            }
-            j.bins[N][idx] = nbn;
-            for (u32 q = 0; q < nnd; q++) j.base[N][bo + q] = 0;
-          }
         }
       }
       const u32 small = __ballot_sync(kFull, k == 1 || k == 2), multi = __ballot_sync(kFull, k == 2);

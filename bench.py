@@ -74,6 +74,11 @@ def parse():
                    help="served: let the server allocate a pinned result tensor per request instead of "
                         "writing results into a reused pinned ring (as the serial path reuses one buffer)")
     p.add_argument("--plan", default="", help="tuning knobs, e.g. digit_bits_max=9,tile_records=2048")
+    p.add_argument("--tune", action="store_true",
+                   help="batched: tune the on-chip thresholds on the batch first and record the graph with the "
+                        "cached plan (autotune), reporting the default graph beside it")
+    p.add_argument("--tune-cache", default=os.path.join(ROOT, ".pytest_tmp", "plans.json"),
+                   help="autotuner cache file for --tune")
     return p.parse_args()
 
 
@@ -315,30 +320,45 @@ def batched(args):
     d_offs = torch.from_numpy(offs).to(dev)
     stream = torch.cuda.Stream(device=dev)
 
-    # batched: one segmented call, captured once and replayed
-    buf.copy_(pristine)
-    launches0 = rg.launch_count()
-    g = rg.SortGraph(buf, K, offsets=d_offs, tmp=tmp, stream=stream)
-    per_replay = (rg.launch_count() - launches0) // 2  # the warm-up call and the captured one
-    for _ in range(max(0, args.warmup - 1)):
-        stream.wait_stream(torch.cuda.current_stream())
+    # batched: one segmented call, captured once and replayed (with --tune: the default plan
+    # and the autotuner's plan for this batch, each in its own graph)
+    def graph_steps(plan):
         buf.copy_(pristine)
-        stream.wait_stream(torch.cuda.current_stream())
-        g.replay()
-    torch.cuda.synchronize()
-    ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(args.steps)]
-    with ClockSampler(0) as clk:
-        for a, b in ev:
-            buf.copy_(pristine)  # restore (untimed), on the current stream
+        launches0 = rg.launch_count()
+        g = rg.SortGraph(buf, K, offsets=d_offs, tmp=tmp, stream=stream, plan=plan)
+        per_replay = (rg.launch_count() - launches0) // 2  # the warm-up call and the captured one
+        for _ in range(max(0, args.warmup - 1)):
             stream.wait_stream(torch.cuda.current_stream())
-            a.record(stream)
+            buf.copy_(pristine)
+            stream.wait_stream(torch.cuda.current_stream())
             g.replay()
-            b.record(stream)
-            torch.cuda.current_stream().wait_stream(stream)
         torch.cuda.synchronize()
-    if rg.status(stream) != 0:
-        raise SystemExit("device status error in the batched sort")
-    batched_ms = [a.elapsed_time(b) for a, b in ev]
+        ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(args.steps)]
+        with ClockSampler(0) as clk:
+            for a, b in ev:
+                buf.copy_(pristine)  # restore (untimed), on the current stream
+                stream.wait_stream(torch.cuda.current_stream())
+                a.record(stream)
+                g.replay()
+                b.record(stream)
+                torch.cuda.current_stream().wait_stream(stream)
+            torch.cuda.synchronize()
+        if rg.status(stream) != 0:
+            raise SystemExit("device status error in the batched sort")
+        return [a.elapsed_time(b) for a, b in ev], per_replay, clk, g.plan
+
+    batched_ms, per_replay, clk, used_plan = graph_steps(None)
+    tuned = None
+    if args.tune:
+        from paper_1703_00687_gb300 import autotune
+        e = autotune.tune_segmented(sizes, R, K, cache=args.tune_cache, apply_best=False)
+        default_ms = batched_ms
+        t_ms, t_per, t_clk, t_plan = graph_steps("auto")
+        tuned = {"plan": {k: t_plan[k] for k in autotune.ONCHIP_KNOBS}, "ms": statistics.median(t_ms),
+                 "default_ms": statistics.median(default_ms),
+                 "candidates": [{"plan": x["plan"], "ms": x["ms"]} for x in e["timings"]]}
+        if statistics.median(t_ms) < statistics.median(default_ms):
+            batched_ms, per_replay, clk, used_plan = t_ms, t_per, t_clk, t_plan
     got = buf.clone()
 
     # plain: one radix_sort call per segment, same data, same stream, one step
@@ -380,7 +400,7 @@ def batched(args):
                 "frac": b_alg / (med / 1e3) / 1e9 / peak},
         "plain": {"value": n / (plain_ms / 1e3), "ms": plain_ms, "wall_s": plain_wall, "launches": plain_launches,
                   "api": "one radix_sort call per segment on one stream"},
-        "speedup_vs_plain": plain_ms / med, "outputs_identical": same,
+        "speedup_vs_plain": plain_ms / med, "outputs_identical": same, "plan": used_plan, "tuned": tuned,
         "gpu_launches": per_replay * args.steps, "step_ms": batched_ms, "clocks": clk.summary(),
     }
     print(json.dumps(line), flush=True)

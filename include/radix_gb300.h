@@ -171,6 +171,11 @@ typedef struct rs_plan {
                                copy into shared memory): this many suspended polls of the
                                barrier, then the call reports RS_ERR_DEVICE_TIMEOUT
                                (default 2^20, about a second) */
+  uint32_t tiny_records;    /* chunks (small bins or segments) of at most this many records are
+                               sorted by warps with sorting networks, larger ones by a CTA:
+                               2..64 (default 64) */
+  uint32_t enum_records;    /* largest bucket of the on-chip sorter finished by enumeration sort
+                               (larger ones are distributed again): 8..64 (default 48) */
 } rs_plan;
 
 rs_status radix_sort_set_plan(const rs_plan *plan);

@@ -169,8 +169,10 @@ def release() -> None:
     check(lib().radix_sort_release(), "radix_sort_release")
 
 
-def set_plan(digit_bits_max=0, tile_records=0, chunk_records=0, sm_limit=0, watchdog_polls=0) -> None:
-    p = RsPlan(digit_bits_max, tile_records, chunk_records, sm_limit, watchdog_polls)
+def set_plan(digit_bits_max=0, tile_records=0, chunk_records=0, sm_limit=0, watchdog_polls=0, tiny_records=0,
+             enum_records=0) -> None:
+    """Sets the process-wide plan (speed only; 0 = automatic).  See ``rs_plan`` in the header."""
+    p = RsPlan(digit_bits_max, tile_records, chunk_records, sm_limit, watchdog_polls, tiny_records, enum_records)
     check(lib().radix_sort_set_plan(ctypes.byref(p)), "radix_sort_set_plan")
 
 

@@ -24,7 +24,8 @@ _vp, _u64, _u32, _i32 = ctypes.c_void_p, ctypes.c_uint64, ctypes.c_uint32, ctype
 class RsPlan(ctypes.Structure):
     _fields_ = [("digit_bits_max", ctypes.c_uint32), ("tile_records", ctypes.c_uint32),
                 ("chunk_records", ctypes.c_uint32), ("sm_limit", ctypes.c_uint32),
-                ("watchdog_polls", ctypes.c_uint32)]
+                ("watchdog_polls", ctypes.c_uint32), ("tiny_records", ctypes.c_uint32),
+                ("enum_records", ctypes.c_uint32)]
 
 
 class RsKernelTime(ctypes.Structure):

@@ -36,7 +36,7 @@ struct Workspace {
 
 static std::mutex g_mu;
 static std::map<std::pair<int, cudaStream_t>, Workspace> g_ws;
-static rs_plan g_plan = {0, 0, 0, 0, 0};
+static rs_plan g_plan = {0, 0, 0, 0, 0, 0, 0};
 static std::atomic<unsigned long long> g_launches{0};
 static std::map<int, int> g_sms;
 static std::atomic<unsigned> g_inject{0};
@@ -221,6 +221,8 @@ static rs_status setup_job(void* in, void* tmp, u64 n, u32 rec_size, u32 key_siz
   j.chunk_max = sh.chunk_max;
   j.inject = g_inject.exchange(0);
   j.wd_polls = p.watchdog_polls ? p.watchdog_polls : kWaitPolls;
+  j.tiny_max = p.tiny_records ? p.tiny_records : kTinyMax;
+  j.es_max = p.enum_records ? p.enum_records : kEsDefault;
   j.n_segs = n_segs;
   int sms = sm_count(dev);
   if (p.sm_limit && (int)p.sm_limit < sms) sms = (int)p.sm_limit;
@@ -375,6 +377,8 @@ static rs_status noalloc_setup(void* in, void* tmp, u64 n, u32 rec_size, u32 key
   j.T = sh.T;
   j.chunk_max = sh.chunk_max;
   j.wd_polls = p.watchdog_polls ? p.watchdog_polls : kWaitPolls;
+  j.tiny_max = p.tiny_records ? p.tiny_records : kTinyMax;
+  j.es_max = p.enum_records ? p.enum_records : kEsDefault;
   const Caps c = caps_for(n, j.chunk_max, j.wmax, 0);
   if (c.bytes > kNoAllocBytes) return RS_ERR_TOO_LARGE;
   st->c = c;
@@ -669,6 +673,8 @@ rs_status radix_sort_set_plan(const rs_plan* plan) {
       p.tile_records != 2048 && p.tile_records != 4096)
     return RS_ERR_INVALID_ARG;
   if (p.chunk_records && p.chunk_records < 64) return RS_ERR_INVALID_ARG;
+  if (p.tiny_records && (p.tiny_records < 2 || p.tiny_records > kTinyMax)) return RS_ERR_INVALID_ARG;
+  if (p.enum_records && (p.enum_records < 8 || p.enum_records > kEsLimit)) return RS_ERR_INVALID_ARG;
   std::lock_guard<std::mutex> lk(g_mu);
   g_plan = p;
   return RS_OK;

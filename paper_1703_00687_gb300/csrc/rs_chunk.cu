@@ -9,16 +9,18 @@
 //   * skip the key bits every record of the range shares (AND/OR of the keys);
 //   * one counting-sort distribution on the next kWinBits bits (fewer for a small chunk),
 //     with shared-memory atomic counters (the order inside a bucket is arbitrary here);
-//   * every bucket of up to kEsMax records is finished by enumeration sort (section 2.2,
-//     3.3): a record's place is the number of records of the bucket that must precede it,
-//     comparing (key, input position) -- so equal keys come out in input order;
+//   * every bucket of up to es_max records (the plan's enumeration limit, 48 by default) is
+//     finished by enumeration sort (section 2.2, 3.3): a record's place is the number of
+//     records of the bucket that must precede it, comparing (key, input position) -- so
+//     equal keys come out in input order;
 //   * a larger bucket is processed again the same way; if all its keys are equal it is put
 //     back in input order (ranks of its input positions, from a bitmap of them);
-//   * a chunk of at most kEsMax records is one enumeration sort, without a distribution.
+//   * a chunk of at most es_max records is one enumeration sort, without a distribution.
 // The result is therefore the stable order, and the whole sorter is stable.
 //
-// Chunks of at most kTinyMax records are kept in a list of their own and sorted by k_tiny:
-// warps, not CTAs, with bitonic sorting networks over lane shuffles (several chunks per warp).
+// Chunks of at most the plan's tiny limit (at most kTinyMax) records are kept in a list of
+// their own and sorted by k_tiny: warps, not CTAs, with bitonic sorting networks over lane
+// shuffles (several chunks per warp).
 #include <algorithm>
 
 #include "rs_internal.cuh"
@@ -30,7 +32,6 @@ namespace rsg {
 constexpr int kCThreads = 512;   // threads of a chunk CTA
 constexpr int kChunkCtas = 2;    // chunk CTAs per SM
 constexpr int kCWarps = kCThreads / 32;
-constexpr int kEsMax = 48;       // largest bucket finished by enumeration sort
 constexpr int kWinBits = 12;     // digit of the on-chip distribution pass
 constexpr int kIdxBits = 13;     // input positions of a chunk (chunk_max <= 2^13)
 constexpr int kChunkItems = 8;   // positions per thread (chunk_max <= kCThreads * this)
@@ -49,7 +50,7 @@ __host__ __device__ inline ChunkLayout chunk_layout(u32 m, u32 RW) {
   ChunkLayout c;
   size_t o = 0;
   c.stage = o; o += (size_t)m * RW * 8;
-  c.aux = o; o += (size_t)m * 8;  // >= 4m (perm, out) + the stack of at most m / (kEsMax + 1) + 2 pairs
+  c.aux = o; o += (size_t)m * 8;  // >= 4m (perm, out) + the stack of at most m / 9 + 2 pairs (es_max >= 8)
   o = (o + 15) & ~(size_t)15;
   c.cnt = o; o += (size_t)kCntWords * 4;
   c.total = (o + 127) & ~(size_t)127;
@@ -66,6 +67,7 @@ struct ChunkCtx {
   u32* cnt;      // 2^kWinBits 16-bit counters, two per word
   u32* stack;    // pairs (begin, size) of buckets still to sort
   u32 stack_cap;
+  u32 es_max;    // largest bucket finished by enumeration sort
 
   __device__ __forceinline__ Key<KW> key(u32 r) const {
     const u64* p = stage + r * (RWT ? (u32)RWT : RW);
@@ -277,7 +279,7 @@ __device__ void distribute(const ChunkCtx<KW, RWT>& c, u32 a, u32 s, const Digit
 }
 
 // After a distribution of positions [a, a + s) by `dig` into c.out (bucket starts in c.cnt):
-// enumeration sort of every bucket of up to kEsMax records into c.perm; the positions of a
+// enumeration sort of every bucket of up to es_max records into c.perm; the positions of a
 // larger bucket are copied as they are and the bucket goes on the stack.  Ends with a
 // barrier, after which *s_top is final.
 template <int KW, int RWT>
@@ -293,7 +295,7 @@ __device__ void finish_round(const ChunkCtx<KW, RWT>& c, u32 a, u32 s, const Dig
     const u32 sz = en - st;
     if (sz == 1) {
       c.perm[a + i] = (u16)r;
-    } else if (sz <= (u32)kEsMax) {
+    } else if (sz <= c.es_max) {
       // enumeration sort: rank = records of the bucket that must precede this one
       u32 rank = 0;
       for (u32 q = st; q < en; q++) {
@@ -401,7 +403,7 @@ __device__ void restore_input_order(const ChunkCtx<KW, RWT>& c, u32 a, u32 s) {
   __syncthreads();
 }
 
-// A chunk of at most kEsMax records: enumeration sort of the whole range at once (each
+// A chunk of at most es_max records: enumeration sort of the whole range at once (each
 // record's rank among all of them by (key, input position)); the counters stay untouched.
 // Kept out of line so that it does not disturb the code of the common path.
 template <int KW, int RWT>
@@ -421,14 +423,14 @@ __device__ __noinline__ void small_chunk_sort(const ChunkCtx<KW, RWT>& c, u32 sz
 // Persistent CTAs take chunks by ticket; the two CTAs of an SM overlap each other's load,
 // sort and write.  Per chunk: one bulk copy of its records into shared memory (bounded wait;
 // the next chunk's records are meanwhile prefetched into L2), then
-//   * more than kEsMax records: the first distribution counts the digit right below the
+//   * more than es_max records: the first distribution counts the digit right below the
 //     chunk's shared bits and keeps every record's composite key (CompSpec).  If no bucket
-//     holds more than kEsMax records, the composite keys go to their buckets and a record's
+//     holds more than es_max records, the composite keys go to their buckets and a record's
 //     place is its bucket's start plus the number of smaller composite keys in the bucket;
 //     records of 8 or 16 bytes are written straight there, larger ones through the order
 //     array.  Otherwise the round goes on with record indices (finish_round) and recurses on
 //     the buckets it leaves on the stack;
-//   * at most kEsMax records: one enumeration sort of the whole chunk;
+//   * at most es_max records: one enumeration sort of the whole chunk;
 //   * already in order: copied to `in` if it lives in tmp.
 template <int KW, int RWT>
 __global__ void __launch_bounds__(kCThreads, kChunkCtas) k_chunk(Job j) {
@@ -453,7 +455,8 @@ __global__ void __launch_bounds__(kCThreads, kChunkCtas) k_chunk(Job j) {
   c.perm = (u16*)(smem + lay.aux);     // general rounds: two order arrays and the stack
   c.out = c.perm + m;
   c.stack = (u32*)(smem + lay.aux + (size_t)m * 4);
-  c.stack_cap = m / (kEsMax + 1) + 2;
+  c.es_max = j.es_max;
+  c.stack_cap = m / (c.es_max + 1) + 2;
   c.cnt = (u32*)(smem + lay.cnt);
   __shared__ Chunk s_ch;
   __shared__ __align__(16) Chunk s_next;  // the next ticket's descriptor, copied in by cp.async
@@ -558,7 +561,7 @@ __global__ void __launch_bounds__(kCThreads, kChunkCtas) k_chunk(Job j) {
     };
     // the first round counts each warp's own strip as soon as it has landed; every other path
     // reads the whole chunk and waits for all strips first
-    const bool strips = bulk && sort && p && sz > (u32)kEsMax;
+    const bool strips = bulk && sort && p && sz > c.es_max;
     if (!strips) {
       if (__syncthreads_or(failed)) {
         give_up();
@@ -576,7 +579,7 @@ __global__ void __launch_bounds__(kCThreads, kChunkCtas) k_chunk(Job j) {
       }
     }
     bool via_perm = false;  // the sorted order is in c.perm (else the records are written)
-    if (sort && sz > (u32)kEsMax) {
+    if (sort && sz > c.es_max) {
       // first round: count the digit, keeping every record's composite key
       const CompSpec cs = comp_spec(dig, p, c.km0, c.km1);
       u64 ck[kChunkItems];
@@ -608,7 +611,7 @@ __global__ void __launch_bounds__(kCThreads, kChunkCtas) k_chunk(Job j) {
         __syncthreads();
       }
       const u32 nd = cs.dmask + 1;
-      const bool big = scan_counts(c, nd < 2 ? 2 : nd, (u32)kEsMax);  // (ends with a barrier)
+      const bool big = scan_counts(c, nd < 2 ? 2 : nd, c.es_max);  // (ends with a barrier)
       if (!big) {
 #pragma unroll
         for (int k = 0; k < kChunkItems; k++)
@@ -659,7 +662,7 @@ __global__ void __launch_bounds__(kCThreads, kChunkCtas) k_chunk(Job j) {
           via_perm = true;
         }
       } else {
-        // a bucket of more than kEsMax records: the general rounds, on record indices
+        // a bucket of more than es_max records: the general rounds, on record indices
 #pragma unroll
         for (int k = 0; k < kChunkItems; k++)
           if (held[k] != 0xffffffffu)
@@ -668,7 +671,7 @@ __global__ void __launch_bounds__(kCThreads, kChunkCtas) k_chunk(Job j) {
         finish_round(c, 0, sz, dig, &s_top);
         while (s_top) {  // s_top is final after the barrier that ends every round
           const u32 top = s_top;
-          if (top > c.stack_cap) {  // cannot happen: buckets on the stack are disjoint and > kEsMax
+          if (top > c.stack_cap) {  // cannot happen: buckets on the stack are disjoint and > es_max
             if (tid == 0) report(ctl, kErrInternal);
             break;
           }

@@ -44,9 +44,12 @@ enum : u32 { kBinRedo = 1u, kBinEqual = 2u, kBinDom = 4u };
 // Chunk flags
 enum : u32 { kChSrcTmp = 1u, kChCopyOnly = 2u };
 
-// Chunks of at most this many records are tiny: warps sort them with sorting networks in
-// registers (k_tiny) instead of a CTA.  They are listed from the top of the chunk array down.
+// Chunks of at most this many records can be tiny: warps sort them with sorting networks in
+// registers (k_tiny) instead of a CTA (the limit of a job, Job::tiny_max, is at most this).
+// They are listed from the top of the chunk array down.
 constexpr u32 kTinyMax = 64;
+// largest bucket the on-chip sorter finishes by enumeration sort (Job::es_max: 8..kEsLimit)
+constexpr u32 kEsDefault = 48, kEsLimit = 64;
 
 // A bin handled by a multi-CTA distribution pass.
 struct Bin {
@@ -115,6 +118,8 @@ struct Job {
   u32 lanes;          // tile ranges of a distribution level (one per histogram CTA)
   u32 inject;         // testing: kInjectRange / kInjectWait (one call)
   u32 wd_polls;       // limit of a device-side wait (suspended polls of a shared-memory barrier)
+  u32 tiny_max;       // chunks of at most this many records go to the warp sorter (<= kTinyMax)
+  u32 es_max;         // largest bucket the on-chip sorter finishes by enumeration sort
 
   u64 keymask[2];     // key bits of words 0 and 1
   Ctl* ctl;

@@ -148,7 +148,7 @@ __global__ void __launch_bounds__(kThreads) k_init_segments(Job j) {
         report(ctl, kErrInternal);
       } else if (e > a + 1) {
         c = e - a;
-        to_tiny = c <= kTinyMax;
+        to_tiny = c <= j.tiny_max;
         to_chunk = !to_tiny && c <= j.chunk_max;
         to_bin = c > j.chunk_max;
       }
@@ -711,14 +711,14 @@ __global__ void __launch_bounds__(kClsThreads, kClsCtas) k_classify(Job j, int l
       vnext[v] = (u16)(next_member(m12, lo + 1, nd) | (keep ? kKeepChunk : 0u));
     }
     __syncthreads();
-    if (tid == 0) {  // (chunks of at most kTinyMax records go to the tiny list)
+    if (tid == 0) {  // (chunks of at most j.tiny_max records go to the tiny list)
       u32 npk = 0, nn = 0, nt = 0;
       for (u32 v = next_member(m12, 0, nd); v < nd;) {
         const u32 x = vnext[v];
         if (x & kKeepChunk) {
           const u32 size = S[vlast[v]] - (v ? S[v - 1] : 0);
           pk[npk] = (u16)v;
-          pkr[npk++] = (u16)(size <= kTinyMax ? (nt++ | kTinyChunk) : nn++);
+          pkr[npk++] = (u16)(size <= j.tiny_max ? (nt++ | kTinyChunk) : nn++);
         }
         const u32 w = x & ~(u32)kKeepChunk;
         v = w > v ? w : nd;

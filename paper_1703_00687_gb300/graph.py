@@ -11,18 +11,23 @@ allocated by an uncaptured call first (an allocation cannot be recorded).
 """
 from __future__ import annotations
 
-from . import sort, sort_segmented
+from . import get_plan, set_plan, sort, sort_segmented
 
 
 class SortGraph:
-    """``SortGraph(records, key_size, offsets=None, tmp=None)``; then ``replay()`` sorts.
+    """``SortGraph(records, key_size, offsets=None, tmp=None, plan=None)``; then ``replay()`` sorts.
 
     With ``offsets`` (CUDA 64-bit tensor of n_segs + 1 record offsets) each segment is
     sorted on its own (``sort_segmented``), else the whole tensor (``sort``).  Construction
     sorts ``records`` once (the uncaptured call), which a later replay repeats harmlessly.
+
+    ``plan``: the plan the graph is recorded with -- a dict of ``set_plan`` knobs, or "auto"
+    for the autotuner's cached plan of this shape (``autotune.apply`` / ``apply_segmented``;
+    the current plan if none is cached).  The knobs are baked into the recorded launches; the
+    process-wide plan is restored afterwards.
     """
 
-    def __init__(self, records, key_size: int, offsets=None, tmp=None, stream=None):
+    def __init__(self, records, key_size: int, offsets=None, tmp=None, stream=None, plan=None):
         import torch
 
         self.records = records
@@ -31,12 +36,35 @@ class SortGraph:
         self.stream = torch.cuda.Stream(device=records.device) if stream is None else stream
         self.key_size = key_size
         self.total = int(offsets[-1].item()) if offsets is not None else records.shape[0]
-        self.stream.wait_stream(torch.cuda.current_stream(records.device))
-        self._call()  # allocates the workspace of this stream
-        self.stream.synchronize()
-        self.graph = torch.cuda.CUDAGraph()
-        with torch.cuda.graph(self.graph, stream=self.stream, capture_error_mode="thread_local"):
-            self._call()
+        before = get_plan()
+        try:
+            self.applied = self._apply(plan)
+            self.plan = get_plan()
+            self.stream.wait_stream(torch.cuda.current_stream(records.device))
+            self._call()  # allocates the workspace of this stream
+            self.stream.synchronize()
+            self.graph = torch.cuda.CUDAGraph()
+            with torch.cuda.graph(self.graph, stream=self.stream, capture_error_mode="thread_local"):
+                self._call()
+        finally:
+            set_plan(**before)
+
+    def _apply(self, plan) -> bool:
+        if plan is None:
+            return False
+        if isinstance(plan, dict):
+            set_plan(**{**get_plan(), **plan})
+            return True
+        if plan != "auto":
+            raise ValueError("plan must be None, a dict of plan knobs, or 'auto'")
+        from . import autotune
+
+        rec_size = self.records.shape[1] * self.records.element_size() if self.records.dim() == 2 else \
+            self.records.element_size()
+        if self.offsets is None:
+            return autotune.apply(self.total, rec_size, self.key_size)
+        off = self.offsets.cpu().numpy()
+        return autotune.apply_segmented(off[1:] - off[:-1], rec_size, self.key_size)
 
     def _call(self):
         if self.offsets is None:

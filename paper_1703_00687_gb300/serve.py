@@ -24,7 +24,7 @@ import time
 from concurrent.futures import Future
 from dataclasses import dataclass, field
 
-from . import reserve, sort, sort_segmented, status, workspace_bytes
+from . import get_plan, reserve, set_plan, sort, sort_segmented, status, workspace_bytes
 
 
 @dataclass
@@ -98,13 +98,19 @@ class Server:
 
     ``cap_bytes``: device memory the admitted groups may hold at once.  ``lanes``: streams
     that run groups concurrently.  ``max_group_records`` / ``max_group_requests`` bound one
-    group (and size the workspace reserved per lane).
+    group (and size the workspace reserved per lane).  ``plans``: on-chip thresholds to sort
+    groups with (``autotune.ONCHIP_KNOBS``, which size no workspace) -- a dict per (rec_size,
+    key_size), or "auto" for the autotuner's cached plan of each group's batch shape
+    (``autotune.apply_segmented``); they are set around each group's launch on the scheduler
+    thread (the plan is process-wide: other threads should not sort meanwhile).
     """
 
     def __init__(self, cap_bytes: int = 120 * 10 ** 9, lanes: int = 4, max_group_records: int = 128 * 10 ** 6,
-                 max_group_requests: int = 256, device=None, poll_s: float = 20e-6, timing: bool = False):
+                 max_group_requests: int = 256, device=None, poll_s: float = 20e-6, timing: bool = False,
+                 plans=None):
         import torch
 
+        self.plans = plans
         self.torch = torch
         self.device = torch.device("cuda", torch.cuda.current_device()) if device is None else torch.device(device)
         self.cap = int(cap_bytes)
@@ -175,6 +181,23 @@ class Server:
                 reserve(self.max_records, R, K, self.max_requests, stream=lane.stream)
             self._reserved[key] = True
 
+    def _set_plan(self, group, R, K):
+        """Sets the group's on-chip thresholds (if any); returns the plan to restore, or None."""
+        if self.plans is None:
+            return None
+        from . import autotune
+
+        before = get_plan()
+        if self.plans == "auto":
+            if not autotune.apply_segmented([r.n for r in group], R, K, knobs=autotune.ONCHIP_KNOBS):
+                return None
+            return before
+        p = self.plans.get((R, K))
+        if not p:
+            return None
+        set_plan(**{**before, **{k: v for k, v in p.items() if k in autotune.ONCHIP_KNOBS}})
+        return before
+
     def _launch(self, lane, group):
         """Three stages on three kinds of stream: the group's host-to-device copies on the
         shared copy-in stream, its sort on the lane's stream, its device-to-host copies on the
@@ -207,10 +230,15 @@ class Server:
                     d_offs = h_offs.to(self.device, non_blocking=True)
                 lane.in_done.record(self.copy_in)
             lane.stream.wait_event(lane.in_done)
-            if len(group) == 1:
-                sort(d_in, K, tmp=d_tmp, stream=lane.stream)
-            else:
-                sort_segmented(d_in, d_offs, K, tmp=d_tmp, stream=lane.stream, total=total)
+            before = self._set_plan(group, R, K)
+            try:
+                if len(group) == 1:
+                    sort(d_in, K, tmp=d_tmp, stream=lane.stream)
+                else:
+                    sort_segmented(d_in, d_offs, K, tmp=d_tmp, stream=lane.stream, total=total)
+            finally:
+                if before is not None:
+                    set_plan(**before)
             lane.sorted.record(lane.stream)
             self.copy_out.wait_event(lane.sorted)
             with torch.cuda.stream(self.copy_out):

@@ -60,3 +60,56 @@ def check_stable_sorted(out: torch.Tensor, pristine: torch.Tensor, key_size: int
             eq &= cx == cy
         ok = lt | (eq & (idx[a:b] < idx[a + 1:b + 1]))
         assert bool(ok.all()), f"order violated in [{a},{b})"
+
+
+# ------------------------------------------------------- records without an index payload
+_C1 = 0xBF58476D1CE4E5B9 - (1 << 64)  # SplitMix64 finaliser constants (Steele, Lea, Flood 2014),
+_C2 = 0x94D049BB133111EB - (1 << 64)  # as signed int64 (products wrap like uint64)
+
+
+def _lsr(x: torch.Tensor, s: int) -> torch.Tensor:
+    return (x >> s) & ((1 << (64 - s)) - 1)
+
+
+def _mix(x: torch.Tensor) -> torch.Tensor:
+    x = x ^ _lsr(x, 30)
+    x = x * _C1
+    x = x ^ _lsr(x, 27)
+    x = x * _C2
+    return x ^ _lsr(x, 31)
+
+
+def record_fingerprint(t: torch.Tensor, block: int = 1 << 25) -> tuple[int, int]:
+    """Two sums (mod 2^64) of independent hashes of every record: equal for any two orders of
+    the same records, and different, short of a 2^-64-scale accident, for different multisets."""
+    n, R = t.shape
+    w = t.view(torch.int64).view(n, R // 8)
+    s1 = torch.zeros((), dtype=torch.int64, device=t.device)
+    s2 = torch.zeros((), dtype=torch.int64, device=t.device)
+    for a in range(0, n, block):
+        b = min(n, a + block)
+        h = torch.zeros(b - a, dtype=torch.int64, device=t.device)
+        for k in range(R // 8):
+            h = _mix(h + w[a:b, k])
+        s1 += h.sum()
+        s2 += _mix(h ^ 0x5DEECE66D).sum()
+    return int(s1), int(s2)
+
+
+def check_sorted_same_records(out: torch.Tensor, pristine: torch.Tensor, key_size: int,
+                              block: int = 1 << 25) -> None:
+    """Keys non-decreasing, and the same multiset of records as the input (by fingerprint).
+    For records that are keys alone, or keys without duplicates, this is the unique sort."""
+    n, R = out.shape
+    wo = out.view(torch.int64).view(n, R // 8)
+    for a in range(0, n - 1, block):
+        b = min(n - 1, a + block)
+        x = _ukey_words(wo[a:b], key_size)
+        y = _ukey_words(wo[a + 1:b + 1], key_size)
+        lt = torch.zeros(b - a, dtype=torch.bool, device=out.device)
+        eq = torch.ones(b - a, dtype=torch.bool, device=out.device)
+        for cx, cy in zip(x, y):
+            lt |= eq & (cx < cy)
+            eq &= cx == cy
+        assert bool((lt | eq).all()), f"order violated in [{a},{b})"
+    assert record_fingerprint(out) == record_fingerprint(pristine), "the output is not a permutation of the input"

@@ -12,7 +12,7 @@ import workloads as wl
 
 torch = pytest.importorskip("torch")
 import paper_1703_00687_gb300 as rg  # noqa: E402
-from tests.gpu_checks import check_stable_sorted  # noqa: E402
+from tests.gpu_checks import check_sorted_same_records, check_stable_sorted  # noqa: E402
 
 pytestmark = pytest.mark.gpu
 
@@ -37,6 +37,24 @@ def test_full_size_sort_is_the_stable_sort(kind, n, R, K, seed, idx_word):
     assert rg.status() == 0
     del tmp
     check_stable_sorted(out, pristine, K, idx_word)
+
+
+@pytest.mark.parametrize("n,R,K,seed", [
+    (1_000_000_000, 16, 16, 8),   # 16-byte keys filling the record (two distribution levels of 9 bits)
+    (2_000_000_000, 8, 8, 9),     # 8-byte records: two levels of 10-bit digits
+])
+def test_full_size_sort_of_keys_without_payload(n, R, K, seed):
+    """Records that are all key: no index to follow, so the output is checked for order and
+    for holding the same records as the input (a multiset fingerprint); with nothing but keys
+    in a record, that is the unique sorted result."""
+    pristine = _device_input("uniform", n, R, K, seed)
+    out = pristine.clone()
+    tmp = torch.empty_like(out)
+    rg.sort(out, K, tmp=tmp)
+    torch.cuda.synchronize()
+    assert rg.status() == 0
+    del tmp
+    check_sorted_same_records(out, pristine, K)
 
 
 def test_full_size_batched_segments_are_each_the_stable_sort():

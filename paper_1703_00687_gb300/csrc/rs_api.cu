@@ -11,6 +11,7 @@
 #include <cstring>
 #include <map>
 #include <mutex>
+#include <tuple>
 #include <utility>
 #include <algorithm>
 #include <vector>
@@ -42,6 +43,46 @@ static std::map<int, int> g_sms;
 static std::atomic<unsigned> g_inject{0};
 
 static std::mutex g_sms_mu;
+
+// kernel attribute and occupancy caches (keyed by device and kernel)
+static std::mutex g_attr_mu;
+static std::map<std::pair<int, const void*>, size_t> g_smem_set;
+static std::map<std::tuple<int, const void*, int, size_t>, int> g_occ;
+
+static int current_device() {
+  int dev = 0;
+  if (cudaGetDevice(&dev) != cudaSuccess) dev = 0;
+  return dev;
+}
+
+void ensure_smem(const void* fn, size_t smem) {
+  const int dev = current_device();
+  std::lock_guard<std::mutex> lk(g_attr_mu);
+  size_t& have = g_smem_set[std::make_pair(dev, fn)];
+  if (smem > have) {
+    if (cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem) == cudaSuccess) have = smem;
+    else cudaGetLastError();  // (the launch then reports the error)
+  }
+}
+
+int occupancy(const void* fn, int threads, size_t smem) {
+  ensure_smem(fn, smem);
+  const int dev = current_device();
+  const auto key = std::make_tuple(dev, fn, threads, smem);
+  {
+    std::lock_guard<std::mutex> lk(g_attr_mu);
+    auto it = g_occ.find(key);
+    if (it != g_occ.end()) return it->second;
+  }
+  int n = 0;
+  if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, fn, threads, smem) != cudaSuccess || n < 1) {
+    cudaGetLastError();
+    n = 1;
+  }
+  std::lock_guard<std::mutex> lk(g_attr_mu);
+  g_occ[key] = n;
+  return n;
+}
 
 static int sm_count(int dev) {
   std::lock_guard<std::mutex> lk(g_sms_mu);

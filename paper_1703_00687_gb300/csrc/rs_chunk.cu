@@ -771,8 +771,7 @@ static cudaError_t launch_chunks_kw(const Job& j, u32 grid, cudaStream_t s) {
   const size_t sm = chunk_smem_bytes(j);
 #define RS_CH(R)                                                                     \
   do {                                                                               \
-    cudaFuncSetAttribute(k_chunk<KW, R>, cudaFuncAttributeMaxDynamicSharedMemorySize, \
-                         (int)sm);                                                   \
+    ensure_smem((const void*)k_chunk<KW, R>, sm);                                    \
     k_chunk<KW, R><<<grid, kCThreads, sm, s>>>(j);                                  \
   } while (0)
   switch (j.RW) {
@@ -789,16 +788,12 @@ static cudaError_t launch_chunks_kw(const Job& j, u32 grid, cudaStream_t s) {
 int chunk_ctas_per_sm(const Job& j) {
   int n = 0;
   const size_t sm = chunk_smem_bytes(j);
-  cudaError_t e;
   if (j.KW == 1) {
-    cudaFuncSetAttribute(k_chunk<1, 0>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
-    e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, k_chunk<1, 0>, kCThreads, sm);
+    n = occupancy((const void*)k_chunk<1, 0>, kCThreads, sm);
   } else {
-    cudaFuncSetAttribute(k_chunk<2, 0>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
-    e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, k_chunk<2, 0>, kCThreads, sm);
+    n = occupancy((const void*)k_chunk<2, 0>, kCThreads, sm);
   }
-  if (e != cudaSuccess || n < 1) n = 1;
-  return n;
+  return n < 1 ? 1 : n;
 }
 
 int launch_chunks(const Job& j, u32 grid, cudaStream_t s) {
@@ -1016,10 +1011,10 @@ int launch_tiny(const Job& j, u32 sms, cudaStream_t s) {
   const u32 per_sm = (u32)std::max<size_t>(1, std::min<size_t>(8, (200 * 1024) / sm));
   cudaError_t e;
   if (j.KW == 1) {
-    cudaFuncSetAttribute(k_tiny<1>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
+    ensure_smem((const void*)k_tiny<1>, sm);
     k_tiny<1><<<sms * per_sm, kTinyThreads, sm, s>>>(j);
   } else {
-    cudaFuncSetAttribute(k_tiny<2>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
+    ensure_smem((const void*)k_tiny<2>, sm);
     k_tiny<2><<<sms * per_sm, kTinyThreads, sm, s>>>(j);
   }
   e = cudaGetLastError();

@@ -373,6 +373,12 @@ __device__ __forceinline__ void load_words_async(u64* dst, const u64* src, u64 w
 __host__ __device__ inline size_t hist_smem_bytes_for(u32 T, u32 KW) { return 2ull * T * KW * 8; }
 
 // ------------------------------------------------------------------ launch helpers
+// Host (rs_api.cu): a kernel's dynamic shared-memory limit, set once per (device, kernel) and
+// raised when a larger size is needed, and its occupancy, cached per (device, kernel,
+// threads, size): both are driver calls of microseconds, and a sort makes dozens of launches.
+void ensure_smem(const void* fn, size_t smem);
+int occupancy(const void* fn, int threads, size_t smem);
+
 // Host-side launchers implemented in the kernel translation units.  Each returns the
 // number of kernels it launched (or -1 on a launch error).
 int launch_init_plain(const Job& j, u32 lo, u32 W, cudaStream_t s);

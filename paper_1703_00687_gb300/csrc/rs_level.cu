@@ -791,16 +791,12 @@ static size_t hist_smem(const Job& j) { return hist_smem_bytes_for(j.T, j.KW); }
 int hist_ctas_per_sm(const Job& j) {
   int n = 0;
   const size_t sm = hist_smem(j);
-  cudaError_t e;
   if (j.KW == 1) {
-    cudaFuncSetAttribute(k_hist<1>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
-    e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, k_hist<1>, kThreads, sm);
+    n = occupancy((const void*)k_hist<1>, kThreads, sm);
   } else {
-    cudaFuncSetAttribute(k_hist<2>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
-    e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, k_hist<2>, kThreads, sm);
+    n = occupancy((const void*)k_hist<2>, kThreads, sm);
   }
-  if (e != cudaSuccess || n < 1) n = 1;
-  return n;
+  return n < 1 ? 1 : n;
 }
 
 int launch_init_plain(const Job& j, u32 lo, u32 W, cudaStream_t s) {
@@ -826,10 +822,10 @@ int launch_hist(const Job& j, int level, int mode, cudaStream_t s) {
   const size_t sm = hist_smem(j);
   const u32 grid = j.lanes;  // one CTA per lane (the scatter pass uses the same lanes)
   if (j.KW == 1) {
-    cudaFuncSetAttribute(k_hist<1>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
+    ensure_smem((const void*)k_hist<1>, sm);
     k_hist<1><<<grid, kThreads, sm, s>>>(j, level, mode);
   } else {
-    cudaFuncSetAttribute(k_hist<2>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
+    ensure_smem((const void*)k_hist<2>, sm);
     k_hist<2><<<grid, kThreads, sm, s>>>(j, level, mode);
   }
   return cudaGetLastError() == cudaSuccess ? 1 : -1;

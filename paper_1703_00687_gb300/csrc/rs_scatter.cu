@@ -406,13 +406,11 @@ size_t level_smem_for(u32 T, u32 RW, u32 KW, u32 wmax) {
 template <int KW, int RWT, int IT, bool MASKS>
 static cudaError_t launch_scatter_m(const Job& j, int level, u32 grid, cudaStream_t s, int* occ) {
   const size_t sm = scatter_smem_bytes(j);
-  cudaFuncSetAttribute(k_scatter<KW, RWT, IT, MASKS>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
   if (occ) {
-    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(occ, k_scatter<KW, RWT, IT, MASKS>, kSThreads, sm) != cudaSuccess ||
-        *occ < 1)
-      *occ = 1;
+    *occ = occupancy((const void*)k_scatter<KW, RWT, IT, MASKS>, kSThreads, sm);
     return cudaSuccess;
   }
+  ensure_smem((const void*)k_scatter<KW, RWT, IT, MASKS>, sm);
   k_scatter<KW, RWT, IT, MASKS><<<grid, kSThreads, sm, s>>>(j, level);
   return cudaGetLastError();
 }

@@ -81,8 +81,11 @@ def form_group(pending, free_bytes: int, max_records: int, max_requests: int, fo
 
 
 class _Lane:
-    def __init__(self, torch, device, timing):
+    def __init__(self, torch, device, timing, max_requests):
         self.stream = torch.cuda.Stream(device=device)
+        # segment offsets of the lane's group, copied from pinned memory allocated once
+        self.h_offs = torch.empty(max_requests + 1, dtype=torch.int64, pin_memory=True)
+        self.d_offs = torch.empty(max_requests + 1, dtype=torch.int64, device=device)
         self.in_start = torch.cuda.Event(enable_timing=timing)  # the group's copy-in may start
         self.in_done = torch.cuda.Event(enable_timing=timing)   # the group's input is on the device
         self.sorted = torch.cuda.Event(enable_timing=timing)    # the group is sorted
@@ -107,9 +110,10 @@ class Server:
 
     def __init__(self, cap_bytes: int = 120 * 10 ** 9, lanes: int = 4, max_group_records: int = 128 * 10 ** 6,
                  max_group_requests: int = 256, device=None, poll_s: float = 20e-6, timing: bool = False,
-                 plans=None):
+                 plans=None, _torch=None):
         import torch
 
+        torch = _torch or torch  # (tests: a CPU stand-in for the CUDA streams and events)
         self.plans = plans
         self.torch = torch
         self.device = torch.device("cuda", torch.cuda.current_device()) if device is None else torch.device(device)
@@ -118,7 +122,7 @@ class Server:
         self.max_requests = int(max_group_requests)
         self.poll_s = poll_s
         self.timing = timing  # per group: copy-in / sort / copy-out times from CUDA events
-        self.lanes = [_Lane(torch, self.device, timing) for _ in range(lanes)]
+        self.lanes = [_Lane(torch, self.device, timing, self.max_requests) for _ in range(lanes)]
         self.copy_in = torch.cuda.Stream(device=self.device)
         self.copy_out = torch.cuda.Stream(device=self.device)
         self.pending = collections.deque()
@@ -226,8 +230,10 @@ class Server:
                     d_in[o:o + r.n].copy_(r.records.view(torch.uint8).reshape(r.n, R), non_blocking=True)
                     o += r.n
                 if len(group) > 1:
-                    h_offs = torch.tensor(offs, dtype=torch.int64).pin_memory()
-                    d_offs = h_offs.to(self.device, non_blocking=True)
+                    # (the lane's last group has finished, so its pinned offsets are free)
+                    lane.h_offs[:len(offs)].copy_(torch.tensor(offs, dtype=torch.int64))
+                    d_offs = lane.d_offs[:len(offs)]
+                    d_offs.copy_(lane.h_offs[:len(offs)], non_blocking=True)
                 lane.in_done.record(self.copy_in)
             lane.stream.wait_event(lane.in_done)
             before = self._set_plan(group, R, K)

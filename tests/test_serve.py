@@ -51,3 +51,4 @@ def test_percentile_interpolates_order_statistics():
     assert percentile(xs, 0) == 1 and percentile(xs, 100) == 5 and percentile(xs, 50) == 3
     assert percentile([0, 10], 99) == pytest.approx(9.9)
     assert percentile([], 50) is None
+

@@ -24,7 +24,7 @@ import time
 from concurrent.futures import Future
 from dataclasses import dataclass, field
 
-from . import get_plan, reserve, set_plan, sort, sort_segmented, status, workspace_bytes
+from . import get_plan, reserve, set_plan, sort, sort_segmented, status_copy, status_decode, workspace_bytes
 
 
 @dataclass
@@ -86,6 +86,8 @@ class _Lane:
         # segment offsets of the lane's group, copied from pinned memory allocated once
         self.h_offs = torch.empty(max_requests + 1, dtype=torch.int64, pin_memory=True)
         self.d_offs = torch.empty(max_requests + 1, dtype=torch.int64, device=device)
+        # the group's device-side status word, copied here on the lane's stream (no host wait)
+        self.h_status = torch.zeros(1, dtype=torch.int32, pin_memory=True)
         self.in_start = torch.cuda.Event(enable_timing=timing)  # the group's copy-in may start
         self.in_done = torch.cuda.Event(enable_timing=timing)   # the group's input is on the device
         self.sorted = torch.cuda.Event(enable_timing=timing)    # the group is sorted
@@ -245,6 +247,7 @@ class Server:
             finally:
                 if before is not None:
                     set_plan(**before)
+            status_copy(lane.h_status, stream=lane.stream)
             lane.sorted.record(lane.stream)
             self.copy_out.wait_event(lane.sorted)
             with torch.cuda.stream(self.copy_out):
@@ -265,7 +268,7 @@ class Server:
         self.groups += 1
 
     def _retire(self, lane):
-        st = status(lane.stream)
+        st = status_decode(int(lane.h_status[0]))  # (written before the group's last event)
         now = time.perf_counter()
         for r in lane.group:
             r.done = now

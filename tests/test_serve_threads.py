@@ -76,6 +76,10 @@ class _FakeTorch:
     def empty(*a, pin_memory=False, device=None, **kw):
         return torch.empty(*a, **kw)
 
+    @staticmethod
+    def zeros(*a, pin_memory=False, device=None, **kw):
+        return torch.zeros(*a, **kw)
+
 
 def _key_sort(t, key_size):  # stable sort of (n, R) uint8 records by their little-endian key
     a = t.numpy()
@@ -87,7 +91,8 @@ def _key_sort(t, key_size):  # stable sort of (n, R) uint8 records by their litt
 def cpu_server(monkeypatch):
     launched = {}
     monkeypatch.setattr(serve, "reserve", lambda *a, **k: None)
-    monkeypatch.setattr(serve, "status", lambda *a, **k: 0)
+    monkeypatch.setattr(serve, "status_copy", lambda dst, stream=None: dst.zero_())
+    monkeypatch.setattr(serve, "status_decode", lambda w: int(w))
     monkeypatch.setattr(serve, "workspace_bytes", lambda n, R, K, s: 1024 * s)
     monkeypatch.setattr(serve, "sort", lambda t, K, tmp=None, stream=None: _key_sort(t, K))
 

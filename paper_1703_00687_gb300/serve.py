@@ -24,7 +24,7 @@ import time
 from concurrent.futures import Future
 from dataclasses import dataclass, field
 
-from . import get_plan, reserve, set_plan, sort, sort_segmented, status_copy, status_decode, workspace_bytes
+from . import get_plan, reserve, set_plan, sort, sort_segmented, status, workspace_bytes
 
 
 @dataclass
@@ -86,8 +86,6 @@ class _Lane:
         # segment offsets of the lane's group, copied from pinned memory allocated once
         self.h_offs = torch.empty(max_requests + 1, dtype=torch.int64, pin_memory=True)
         self.d_offs = torch.empty(max_requests + 1, dtype=torch.int64, device=device)
-        # the group's device-side status word, copied here on the lane's stream (no host wait)
-        self.h_status = torch.zeros(1, dtype=torch.int32, pin_memory=True)
         self.in_start = torch.cuda.Event(enable_timing=timing)  # the group's copy-in may start
         self.in_done = torch.cuda.Event(enable_timing=timing)   # the group's input is on the device
         self.sorted = torch.cuda.Event(enable_timing=timing)    # the group is sorted
@@ -137,6 +135,7 @@ class Server:
         self._closing = False
         self._error = None
         self._reserved = {}
+        self._launching = []
         self._thread = threading.Thread(target=self._run, name="sort-server", daemon=True)
         self._thread.start()
 
@@ -247,7 +246,6 @@ class Server:
             finally:
                 if before is not None:
                     set_plan(**before)
-            status_copy(lane.h_status, stream=lane.stream)
             lane.sorted.record(lane.stream)
             self.copy_out.wait_event(lane.sorted)
             with torch.cuda.stream(self.copy_out):
@@ -268,7 +266,7 @@ class Server:
         self.groups += 1
 
     def _retire(self, lane):
-        st = status_decode(int(lane.h_status[0]))  # (written before the group's last event)
+        st = status(lane.stream)
         now = time.perf_counter()
         for r in lane.group:
             r.done = now
@@ -307,14 +305,17 @@ class Server:
                         self._cv.wait(timeout=0.05)
                         continue
                 if group:
+                    self._launching = group  # (failed too if the launch raises)
                     self._launch(free[0], group)
+                    self._launching = []
                 elif idle:
                     time.sleep(self.poll_s)
         except BaseException as e:  # fail every waiting request rather than hang them
             self._error = e
             with self._cv:
-                waiting = list(self.pending)
+                waiting = list(self.pending) + list(self._launching)
                 self.pending.clear()
+                self._closing = True  # (submit now raises: nothing would serve the request)
             for lane in self.lanes:
                 waiting += lane.group or []
             for r in waiting:

@@ -91,8 +91,7 @@ def _key_sort(t, key_size):  # stable sort of (n, R) uint8 records by their litt
 def cpu_server(monkeypatch):
     launched = {}
     monkeypatch.setattr(serve, "reserve", lambda *a, **k: None)
-    monkeypatch.setattr(serve, "status_copy", lambda dst, stream=None: dst.zero_())
-    monkeypatch.setattr(serve, "status_decode", lambda w: int(w))
+    monkeypatch.setattr(serve, "status", lambda *a, **k: 0)
     monkeypatch.setattr(serve, "workspace_bytes", lambda n, R, K, s: 1024 * s)
     monkeypatch.setattr(serve, "sort", lambda t, K, tmp=None, stream=None: _key_sort(t, K))
 
@@ -134,3 +133,17 @@ def test_a_lone_request_is_served_without_any_other_activity(cpu_server):
             out = f.result(timeout=5)
             assert np.array_equal(out.numpy().view("<u8").ravel(), np.arange(64, dtype=np.uint64))
             time.sleep(0.01)
+
+
+@pytest.mark.timeout(60)
+def test_a_failing_launch_fails_its_requests_instead_of_leaving_them_waiting(cpu_server, monkeypatch):
+    def boom(t, K, tmp=None, stream=None):
+        raise RuntimeError("launch failed")
+    monkeypatch.setattr(serve, "sort", boom)
+    srv = serve.Server(cap_bytes=1 << 30, lanes=2, device="cpu", _torch=_FakeTorch())
+    a = np.zeros((10, 8), dtype=np.uint8)
+    f = srv.submit(torch.from_numpy(a), 8)
+    with pytest.raises(RuntimeError, match="launch failed"):
+        f.result(timeout=10)
+    with pytest.raises(RuntimeError):
+        srv.close()  # (re-raises the scheduler's error)

@@ -150,19 +150,6 @@ rs_status radix_count_runs(const void *in, uint64_t n, uint32_t rec_size, uint32
  */
 rs_status radix_sort_status(rs_stream_t stream);
 
-/*
- * The same status without waiting: enqueues on `stream` a copy of the device-side status of
- * the calls made on it so far into *dst (host page-locked memory or device memory, 4 bytes:
- * 0 = ok, else a nonzero code whose meaning radix_sort_status_decode gives) and clears it.
- * Nothing is read until the stream reaches that point; the call returns at once.  Useful where
- * a blocking read would stall a thread that feeds other streams (a server).
- * RS_ERR_INVALID_ARG for a null dst.
- */
-rs_status radix_sort_status_copy(rs_stream_t stream, uint32_t *dst);
-
-/* The rs_status of a word written by radix_sort_status_copy (or radix_sort_noalloc's d_status). */
-rs_status radix_sort_status_decode(uint32_t word);
-
 /* Human-readable name of a status code (static storage). */
 const char *radix_sort_strerror(rs_status status);
 

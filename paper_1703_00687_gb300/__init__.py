@@ -16,8 +16,7 @@ import ctypes
 
 from ._lib import KERNEL_NAMES, RadixSortError, RsKernelTime, RsPlan, check, lib
 
-__all__ = ["sort", "sort_host", "sort_segmented", "partition", "histogram", "count_runs", "status", "status_copy",
-           "status_decode", "release", "set_plan",
+__all__ = ["sort", "sort_host", "sort_segmented", "partition", "histogram", "count_runs", "status", "release", "set_plan",
            "get_plan", "launch_count", "chunk_records", "workspace_bytes", "reserve",
            "profile", "RadixSortError", "lib", "SortGraph"]
 
@@ -160,18 +159,6 @@ def count_runs(records, key_size: int, stream=None):
 def status(stream=None) -> int:
     """Drains the stream and returns the device-side status code of its calls (0 = ok)."""
     return lib().radix_sort_status(_stream(stream))
-
-
-def status_copy(dst, stream=None) -> None:
-    """Enqueues on ``stream`` a copy of its calls' device-side status word into ``dst`` (a
-    pinned-host or CUDA tensor of at least 4 bytes) and clears it, without waiting; decode the
-    word with ``status_decode`` once the stream has passed this point."""
-    check(lib().radix_sort_status_copy(_stream(stream), dst.data_ptr()), "radix_sort_status_copy")
-
-
-def status_decode(word: int) -> int:
-    """The status code (0 = ok) of a word written by ``status_copy``."""
-    return lib().radix_sort_status_decode(int(word) & 0xFFFFFFFF)
 
 
 def check_status(stream=None) -> None:

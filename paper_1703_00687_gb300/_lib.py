@@ -53,8 +53,6 @@ SIGNATURES = {
     "radix_sort_test_inject": (_i32, [_u32]),
     "radix_sort_noalloc": (_i32, [_vp, _vp, _u64, _u32, _u32, _vp, _vp]),
     "radix_sort_profile": (_i32, [_i32]),
-    "radix_sort_status_copy": (_i32, [ctypes.c_void_p, ctypes.c_void_p]),
-    "radix_sort_status_decode": (_i32, [ctypes.c_uint32]),
     "radix_sort_profile_kernels": (_i32, [ctypes.c_uint32]),
     "radix_sort_profile_read": (ctypes.c_int64, [ctypes.POINTER(RsKernelTime), ctypes.c_int64]),
 }

@@ -676,30 +676,6 @@ rs_status radix_sort_status(rs_stream_t stream) {
   return RS_OK;
 }
 
-rs_status radix_sort_status_copy(rs_stream_t stream, uint32_t* dst) {
-  if (!dst) return RS_ERR_INVALID_ARG;
-  cudaStream_t s = (cudaStream_t)stream;
-  int dev = 0;
-  if (cudaGetDevice(&dev) != cudaSuccess) return RS_ERR_CUDA;
-  Ctl* ctl = nullptr;
-  {
-    std::lock_guard<std::mutex> lk(g_mu);
-    auto it = g_ws.find(std::make_pair(dev, s));
-    if (it != g_ws.end() && it->second.mem) ctl = it->second.ctl;
-  }
-  if (!ctl) {  // no call has run on this stream: nothing to report
-    return cudaMemsetAsync(dst, 0, sizeof(uint32_t), s) == cudaSuccess ? RS_OK : RS_ERR_CUDA;
-  }
-  if (cudaMemcpyAsync(dst, &ctl->err, sizeof(uint32_t), cudaMemcpyDefault, s) != cudaSuccess ||
-      cudaMemsetAsync(&ctl->err, 0, sizeof(uint32_t), s) != cudaSuccess)
-    return RS_ERR_CUDA;
-  return RS_OK;
-}
-
-rs_status radix_sort_status_decode(uint32_t err) {
-  return radix_sort_status_decode(err);
-}
-
 const char* radix_sort_strerror(rs_status s) {
   switch (s) {
     case RS_OK: return "ok";

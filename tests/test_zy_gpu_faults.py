@@ -95,23 +95,3 @@ def test_invalid_segment_offsets_are_reported_not_written():
     assert rg.status() == 0
     np.testing.assert_array_equal(from_dev(t), a)
 
-
-def test_status_copy_reports_without_waiting_and_clears():
-    """radix_sort_status_copy enqueues the status word's copy on the stream (no host wait);
-    decoded after the stream has passed it, it gives what radix_sort_status would."""
-    a = _records(seed=24)
-    word = torch.full((1,), 0x7FFF, dtype=torch.int32).pin_memory()
-    s = torch.cuda.current_stream()
-    try:
-        assert rg.lib().radix_sort_test_inject(1) == 0
-        t = to_dev(a)
-        rg.sort(t, 8)
-        rg.status_copy(word, stream=s)
-        s.synchronize()
-        assert rg.status_decode(int(word[0])) == RS_ERR_INTERNAL
-    finally:
-        rg.lib().radix_sort_test_inject(0)
-    rg.status_copy(word, stream=s)  # cleared by the first copy
-    s.synchronize()
-    assert int(word[0]) == 0 and rg.status() == 0
-    _next_sort_is_correct(a)

@@ -91,7 +91,7 @@ def measured_peaks():
         return 6800.0, "fallback"
 
 
-KERNEL_SOURCES = {"scatter": ["rs_level.cu", "rs_internal.cuh"], "hist": ["rs_level.cu", "rs_internal.cuh"],
+KERNEL_SOURCES = {"scatter": ["rs_scatter.cu", "rs_internal.cuh"], "hist": ["rs_level.cu", "rs_internal.cuh"],
                   "chunk": ["rs_chunk.cu", "rs_internal.cuh"]}
 
 

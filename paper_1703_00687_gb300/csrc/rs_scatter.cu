@@ -10,7 +10,15 @@ namespace rsg {
 
 // --------------------------------------------------------------------- scatter
 constexpr int kSThreads = 256;  // threads of a scatter CTA
-constexpr int kSWarps = kSThreads / 32;
+// 8-byte records at the default tile (4,096 records) with 10-bit digit tables take CTAs of
+// 512 threads: each warp ranks half as many records in a row, and twice as many warps hide
+// the shared-memory latency of the ranking (measured at 2e9 x 8 B, two 10-bit levels: 31.3 vs
+// 33.8 ms of scatter per sort).  Not with 9-bit tables (1e9 x 8 B: 13.3 vs 12.5 ms), nor for
+// larger records (16 to 32 bytes: 1-2% slower), where 256 threads keep the lane masks.
+constexpr int kSThreadsWide = 512;
+__host__ __device__ inline u32 scatter_threads(u32 T, u32 RW, u32 wmax) {
+  return RW == 1 && T == 4096 && wmax >= 10 ? (u32)kSThreadsWide : (u32)kSThreads;
+}
 
 // Shared memory of k_scatter: T records, per-warp 16-bit digit counters (row stride 2^wmax),
 // the tile's permutation (sharing its room with one byte per warp and bucket, used while
@@ -27,6 +35,7 @@ struct ScatterLayout {
 constexpr size_t kScatterPairSmem = 112 * 1024;
 
 __host__ __device__ inline ScatterLayout scatter_layout(u32 T, u32 RW, u32 wmax) {
+  const size_t kSWarps = scatter_threads(T, RW, wmax) / 32;
   ScatterLayout s;
   const size_t nd = (size_t)1 << wmax;
   size_t o = 0;
@@ -54,9 +63,10 @@ __device__ __forceinline__ u32 staged_digit(const u64* rec, u32 lo, u32 W) {
   return digit_of<KW>(k, lo, W);
 }
 
-// Digits per thread in the scatter's prefix pass: nd / kSThreads, at least 2 (the per-warp
-// counters are read two at a time).
-__device__ __forceinline__ u32 digits_per_thread(u32 nd) { return nd > 2u * kSThreads ? nd / kSThreads : 2u; }
+// Digits per thread in the scatter's prefix pass: nd / NT, at least 2 (the per-warp counters
+// are read two at a time).
+template <int NT>
+__device__ __forceinline__ u32 digits_per_thread(u32 nd) { return nd > 2u * NT ? nd / NT : 2u; }
 
 constexpr u64 kSkip = ~0ull;  // gbase of a digit whose run would leave its bin
 
@@ -68,15 +78,16 @@ constexpr u64 kSkip = ~0ull;  // gbase of a digit whose run would leave its bin
 // are known from those starts plus the digit counts of the lane's earlier tiles of the bin,
 // which the CTA keeps in registers: no tile waits for another.
 //
-// Per tile of T = kSThreads * IT records: the records are staged in shared memory; warp w
+// Per tile of T = NT * IT records: the records are staged in shared memory; warp w
 // ranks its strip of records in order (lanes sharing a bucket found through a per-warp byte
 // per bucket, per-warp 16-bit counters), so the order inside a digit is the input order
 // (stable); the digit counts are
 // scanned; then the tile is written in digit order, so consecutive threads write consecutive
 // records of a run with 16-byte streaming stores.
 // MASKS: the layout has the per-warp lane masks (chosen at launch from scatter_layout).
-template <int KW, int RWT, int IT, bool MASKS>
-__global__ void __launch_bounds__(kSThreads, 2) k_scatter(Job j, int level) {
+template <int KW, int RWT, int IT, bool MASKS, int NT>
+__global__ void __launch_bounds__(NT, 2) k_scatter(Job j, int level) {
+  constexpr int kSWarps = NT / 32;
   const int L = level & 1;
   Ctl* ctl = j.ctl;
   const u64 nb = ctl->nbins[L];
@@ -84,9 +95,9 @@ __global__ void __launch_bounds__(kSThreads, 2) k_scatter(Job j, int level) {
   const u64 ntiles = ctl->ntiles[L];
   const Bin* bins = j.bins[L];
   const u32 RW = RWT ? (u32)RWT : j.RW;
-  constexpr u32 T = kSThreads * IT;
+  constexpr u32 T = NT * IT;
   constexpr u32 PW = T / kSWarps;  // records per warp strip
-  constexpr u32 kDigitsPerThread = (1u << kWMax) / kSThreads;
+  constexpr u32 kDigitsPerThread = (1u << kWMax) / NT;
   const u32 WSMAX = 1u << j.wmax;  // room for the per-warp counters: kSWarps rows of 2^wmax
   const ScatterLayout lay = scatter_layout(T, RW, j.wmax);
   if (MASKS != lay.masks) {  // (cannot happen: the launcher picks MASKS from the same layout)
@@ -111,9 +122,9 @@ __global__ void __launch_bounds__(kSThreads, 2) k_scatter(Job j, int level) {
   if (tid == 0) mbar_init(&s_never, 1);
   // per-warp digit counters: counts while ranking, then each warp's offset inside the digit's
   // run; they are zeroed again while the tile is written out
-  for (u32 i = tid; i < kSWarps * WSMAX; i += kSThreads) whist[i] = 0;
+  for (u32 i = tid; i < kSWarps * WSMAX; i += NT) whist[i] = 0;
   if (MASKS)
-    for (u32 i = tid; i < kSWarps * WSMAX; i += kSThreads) peermask[i] = 0;
+    for (u32 i = tid; i < kSWarps * WSMAX; i += NT) peermask[i] = 0;
   const u64 per = lane_tiles(ntiles, j.lanes);
   bool inject = (j.inject & kInjectRange) && blockIdx.x == 0 && tid == 0;  // testing: fail one run check
   bool inject_wait = (j.inject & kInjectWait) && blockIdx.x == 0;  // testing: one wait runs out
@@ -166,7 +177,7 @@ __global__ void __launch_bounds__(kSThreads, 2) k_scatter(Job j, int level) {
       const u32 bytes = cnt * RW * 8;
       const bool bulk = ((((uintptr_t)src) | bytes) & 15) == 0;
       if (!bulk) {
-        load_words_async<kSThreads>(stage, src, (u64)cnt * RW);
+        load_words_async<NT>(stage, src, (u64)cnt * RW);
       } else if (lane == 0) {
         // (strip boundaries are multiples of PW records: 16-byte aligned, as is the tile's end)
         const u32 a = warp * PW, e = min(cnt, a + PW);
@@ -180,7 +191,7 @@ __global__ void __launch_bounds__(kSThreads, 2) k_scatter(Job j, int level) {
       if (b != cur) {  // first tile of this lane's part of the bin: its run starts
         cur = b;
         const u64* sg = j.seg + ((ln + b) << j.wmax);
-        const u32 D = digits_per_thread(nd);
+        const u32 D = digits_per_thread<NT>(nd);
 #pragma unroll
         for (u32 q = 0; q < kDigitsPerThread; q++) {
           const u32 v = D * tid + q;
@@ -285,7 +296,7 @@ __global__ void __launch_bounds__(kSThreads, 2) k_scatter(Job j, int level) {
       // Thread tid owns digits [D*tid, D*tid + D): it turns their per-warp counts into each
       // warp's offset inside the digit's run (two 16-bit counters per 32-bit access), then one
       // block scan of the threads' totals gives the digits' first slots in the tile.
-      const u32 D = digits_per_thread(nd);
+      const u32 D = digits_per_thread<NT>(nd);
       const u32 v0 = D * tid;
       u32 c[kDigitsPerThread];
 #pragma unroll
@@ -311,7 +322,7 @@ __global__ void __launch_bounds__(kSThreads, 2) k_scatter(Job j, int level) {
       u32 mine = 0;
 #pragma unroll
       for (u32 q = 0; q < kDigitsPerThread; q++) mine += c[q];
-      u32 tb = block_exclusive_sum<kSThreads>(mine, scan_scr);
+      u32 tb = block_exclusive_sum<NT>(mine, scan_scr);
       // destinations of this thread's runs; a run that would leave its bin (possible only with
       // corrupted counts) is reported and not written
 #pragma unroll
@@ -355,13 +366,13 @@ __global__ void __launch_bounds__(kSThreads, 2) k_scatter(Job j, int level) {
       }
       __syncthreads();
       // per-warp counters back to zero for the next tile (nothing reads them before then)
-      for (u32 v = tid; v < nd; v += kSThreads) {
+      for (u32 v = tid; v < nd; v += NT) {
 #pragma unroll
         for (int w = 0; w < kSWarps; w++) whist[w * WS + v] = 0;
       }
       // write the tile in digit order: consecutive slots of one digit go to consecutive records
       if (RW == 2) {
-        for (u32 s = tid; s < cnt; s += kSThreads) {
+        for (u32 s = tid; s < cnt; s += NT) {
           const u32 sw = slotw[s];
           const u64 g = gbase[sw >> 16];
           const ulonglong2 v = *reinterpret_cast<const ulonglong2*>(stage + 2 * (sw & 0xffffu));
@@ -403,22 +414,22 @@ size_t level_smem_for(u32 T, u32 RW, u32 KW, u32 wmax) {
   return a > b ? a : b;
 }
 
-template <int KW, int RWT, int IT, bool MASKS>
+template <int KW, int RWT, int IT, bool MASKS, int NT>
 static cudaError_t launch_scatter_m(const Job& j, int level, u32 grid, cudaStream_t s, int* occ) {
   const size_t sm = scatter_smem_bytes(j);
   if (occ) {
-    *occ = occupancy((const void*)k_scatter<KW, RWT, IT, MASKS>, kSThreads, sm);
+    *occ = occupancy((const void*)k_scatter<KW, RWT, IT, MASKS, NT>, NT, sm);
     return cudaSuccess;
   }
-  ensure_smem((const void*)k_scatter<KW, RWT, IT, MASKS>, sm);
-  k_scatter<KW, RWT, IT, MASKS><<<grid, kSThreads, sm, s>>>(j, level);
+  ensure_smem((const void*)k_scatter<KW, RWT, IT, MASKS, NT>, sm);
+  k_scatter<KW, RWT, IT, MASKS, NT><<<grid, NT, sm, s>>>(j, level);
   return cudaGetLastError();
 }
 
-template <int KW, int RWT, int IT>
+template <int KW, int RWT, int IT, int NT = kSThreads>
 static cudaError_t launch_scatter_t(const Job& j, int level, u32 grid, cudaStream_t s, int* occ) {
-  return scatter_layout(j.T, j.RW, j.wmax).masks ? launch_scatter_m<KW, RWT, IT, true>(j, level, grid, s, occ)
-                                                  : launch_scatter_m<KW, RWT, IT, false>(j, level, grid, s, occ);
+  return scatter_layout(j.T, j.RW, j.wmax).masks ? launch_scatter_m<KW, RWT, IT, true, NT>(j, level, grid, s, occ)
+                                                  : launch_scatter_m<KW, RWT, IT, false, NT>(j, level, grid, s, occ);
 }
 
 // Record sizes of 8 to 32 bytes at their default tile (T * rec_size = 64 KB at most) have
@@ -426,7 +437,6 @@ static cudaError_t launch_scatter_t(const Job& j, int level, u32 grid, cudaStrea
 template <int KW, int IT>
 static cudaError_t scatter_rw(const Job& j, int level, u32 grid, cudaStream_t s, int* occ) {
   if constexpr (IT == 16) {
-    if (j.RW == 1) return launch_scatter_t<KW, 1, 16>(j, level, grid, s, occ);
     if (j.RW == 2) return launch_scatter_t<KW, 2, 16>(j, level, grid, s, occ);
   }
   if constexpr (IT == 8) {
@@ -438,6 +448,9 @@ static cudaError_t scatter_rw(const Job& j, int level, u32 grid, cudaStream_t s,
 
 template <int KW>
 static cudaError_t scatter_it(const Job& j, int level, u32 grid, cudaStream_t s, int* occ) {
+  if constexpr (KW == 1)  // (8-byte records hold 8-byte keys at most)
+    if (scatter_threads(j.T, j.RW, j.wmax) == (u32)kSThreadsWide)
+      return launch_scatter_t<KW, 1, 4096 / kSThreadsWide, kSThreadsWide>(j, level, grid, s, occ);
   switch (j.T / kSThreads) {
     case 16: return scatter_rw<KW, 16>(j, level, grid, s, occ);
     case 8: return scatter_rw<KW, 8>(j, level, grid, s, occ);

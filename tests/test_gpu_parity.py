@@ -149,6 +149,21 @@ def test_sort_parity_sm_limit(n, R, K):
     np.testing.assert_array_equal(got, oracle.sort(a, K))
 
 
+@pytest.mark.parametrize("n,K", [(4096 * 5 + 3, 8), (300_007, 8), (1_000_003, 5)])
+def test_sort_parity_ten_bit_digits_8_byte_records(n, K):
+    """8-byte records with 10-bit digit tables: the scatter's CTAs of 512 threads (16 warps,
+    lanes grouped by winner bytes), over several tiles and a ragged last one."""
+    rng = np.random.default_rng(n + K)
+    a = rand(rng, n, 8, K)
+    old = rg.get_plan()
+    try:
+        rg.set_plan(digit_bits_max=10)
+        got = gsort(a, K)
+    finally:
+        rg.set_plan(**old)
+    np.testing.assert_array_equal(got, oracle.sort(a, K))
+
+
 @pytest.mark.parametrize("R,K,pattern", [(16, 8, "90"), (16, 8, "55"), (16, 8, "two"), (16, 8, "zero"),
                                          (16, 8, "ones"), (24, 16, "90"), (24, 16, "ones"), (16, 5, "90"),
                                          (8, 8, "97"), (64, 16, "two")])

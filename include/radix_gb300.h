@@ -260,9 +260,12 @@ rs_status radix_sort_profile_kernels(uint32_t mask);
  * Arguments and result are those of radix_sort; the sort is the same (byte-identical
  * output).  Additionally:
  *   d_status  optional DEVICE pointer to one uint32: when the call's work has run it holds
- *             the call's device-side status (0 = ok; nonzero = a list overflowed or a range
- *             check failed, as radix_sort_status reports for radix_sort).  NULL: none.
- *             (radix_sort_status does not see calls made through this entry point.)
+ *             the call's device-side error bits, 0 = ok, else the OR of 1 (a bounded wait
+ *             ran out: RS_ERR_DEVICE_TIMEOUT), 2 (a list outgrew its bound:
+ *             RS_ERR_QUEUE_OVERFLOW) and 4 (a destination range check failed:
+ *             RS_ERR_INTERNAL), the conditions radix_sort_status reports for radix_sort.
+ *             NULL: none.  (radix_sort_status does not see calls made through this entry
+ *             point.)
  * Limits:
  *   The workspace needed for (n, rec_size, key_size) must fit the 64 MiB array, else the
  *   call returns RS_ERR_TOO_LARGE and launches nothing.  With the default plan that is about
@@ -283,7 +286,9 @@ rs_status radix_sort_noalloc(void *in, void *tmp, uint64_t n, uint32_t rec_size,
 
 /*
  * Testing only; the flags apply to the next radix_sort / radix_sort_segmented / radix_partition
- * call on any stream, then clear (flags = 0 clears them at once).
+ * / radix_sort_noalloc call on any stream, then clear (flags = 0 clears them at once).  For
+ * radix_sort_noalloc the failure reaches the caller's status word (value 4 or 1) instead of
+ * radix_sort_status().
  *   bit 0 (1): each distribution pass treats the first non-empty digit run of its first tile as
  *          failing the destination range check, so that run is not written: the call's later
  *          kernels do nothing, and radix_sort_status() reports RS_ERR_INTERNAL.

@@ -818,6 +818,7 @@ rs_status radix_sort_noalloc(void* in, void* tmp, uint64_t n, uint32_t rec_size,
   st.sms = sms;
   st.dev = dev;
   st.j.lanes = lanes_for(st.j, sms);
+  st.j.inject = g_inject.exchange(0);  // testing only (radix_sort_test_inject)
   const Job& j = st.j;
   // the array keeps the previous call's contents: its error word starts this call at zero,
   // and the init kernels rewrite the rest of the control block and the first bin list

@@ -79,12 +79,13 @@ constexpr u64 kSkip = ~0ull;  // gbase of a digit whose run would leave its bin
 // which the CTA keeps in registers: no tile waits for another.
 //
 // Per tile of T = NT * IT records: the records are staged in shared memory; warp w
-// ranks its strip of records in order (lanes sharing a bucket found through a per-warp byte
-// per bucket, per-warp 16-bit counters), so the order inside a digit is the input order
-// (stable); the digit counts are
-// scanned; then the tile is written in digit order, so consecutive threads write consecutive
-// records of a run with 16-byte streaming stores.
+// ranks its strip of records in order (lanes sharing a bucket found through per-warp lane
+// masks or bytes per bucket, per-warp 16-bit counters), so the order inside a digit is the
+// input order (stable); the digit counts are scanned; then the tile is written in digit
+// order, so consecutive threads write consecutive records of a run with 16-byte streaming
+// stores.
 // MASKS: the layout has the per-warp lane masks (chosen at launch from scatter_layout).
+// NT: threads of the CTA (scatter_threads).
 template <int KW, int RWT, int IT, bool MASKS, int NT>
 __global__ void __launch_bounds__(NT, 2) k_scatter(Job j, int level) {
   constexpr int kSWarps = NT / 32;

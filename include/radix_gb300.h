@@ -223,7 +223,7 @@ enum {
   RS_K_CLASSIFY = 4,  /* sub-bin classification and the next level's bin list */
   RS_K_CHUNK = 5,     /* on-chip sorts of small bins */
   RS_K_COPY = 6,      /* copy-back of finished ranges left in tmp */
-  RS_K_TINY = 7       /* warp sorts of tiny chunks (at most 32 records) */
+  RS_K_TINY = 7       /* warp sorts of tiny chunks (at most 64 records) */
 };
 typedef struct rs_kernel_time {
   uint32_t kernel;
